@@ -1,0 +1,247 @@
+/*
+ * hnv.h -- C ABI of the GB300 HyperNetVec V-cycle library (libhnv.so).
+ *
+ * The library computes the multilevel hypergraph embedding of HyperNetVec
+ * (Maleki, Saless, Wall, Pingali, "HyperNetVec: Fast and Scalable
+ * Hierarchical Embedding for Hypergraphs"): coarsening (Algorithm 1,
+ * Section 3.1), projection and refinement (Algorithm 2, Section 3.3) over the
+ * star expansion of the hypergraph (Section 1.1), run as a V-cycle from the
+ * coarsest level back to the original hypergraph (Section 3, Fig. 1).
+ *
+ * Conventions
+ *  - Every call returns an int: HNV_OK (0) or a negative HNV_ERR_* code.
+ *    Nothing throws across the ABI. hnv_error_string() names a code and
+ *    hnv_last_error_detail() gives a one-line message for the calling
+ *    thread's last failure.
+ *  - Streams are cudaStream_t values passed as hnv_stream_t (ABI-identical;
+ *    NULL = the legacy default stream). Calls are asynchronous on that stream
+ *    unless stated otherwise.
+ *  - Embedding buffers are caller-owned device memory (e.g. torch tensors):
+ *    row-major [rows x d], contiguous, 16-byte aligned, row stride d
+ *    elements. HNV_F32 needs d % 4 == 0; HNV_BF16 needs d % 8 == 0;
+ *    4 <= d <= 1024.
+ *  - The hierarchy (all levels' incidence arrays and maps) is owned by an
+ *    opaque hnv_graph and released by hnv_graph_free(). Its device memory
+ *    is allocated stream-ordered (cudaMallocAsync) unless an allocator is
+ *    installed with hnv_set_allocator().
+ *  - IDs are int32: n, m < 2^31 and every level's incidence count
+ *    nnz < 2^31 (HNV_ERR_TOO_LARGE otherwise).
+ */
+#ifndef HNV_H_
+#define HNV_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ABI-identical to cudaStream_t. */
+typedef struct CUstream_st* hnv_stream_t;
+
+/* Error codes. */
+enum {
+  HNV_OK = 0,
+  HNV_ERR_INVALID_ARG = -1,   /* bad pointer, size, weight, enum or layout */
+  HNV_ERR_OUT_OF_RANGE = -2,  /* a node ID >= n in the input, or a level index */
+  HNV_ERR_TOO_LARGE = -3,     /* a count would not fit the int32 index space */
+  HNV_ERR_OOM = -4,           /* device allocation failed */
+  HNV_ERR_CUDA = -5,          /* a CUDA runtime call or kernel launch failed */
+  HNV_ERR_TIMEOUT = -6,       /* a bounded device wait gave up */
+  HNV_ERR_UNSUPPORTED_D = -7, /* embedding width not supported for the dtype */
+  HNV_ERR_STATE = -8          /* call made in the wrong state (e.g. no hierarchy) */
+};
+
+typedef enum { HNV_F32 = 0, HNV_BF16 = 1 } hnv_dtype;
+
+/* Update order of one refinement sweep (Algorithm 2, Section 3.3).
+ * TWO_PHASE: every hyperedge from the current node embeddings, then every
+ *   node from the new hyperedge embeddings (the text's "hyperedges are
+ *   updated using the nodes, and nodes using the hyperedges").
+ * JACOBI: both sides from the previous iterate (Algorithm 2 as printed). */
+typedef enum { HNV_SWEEP_TWO_PHASE = 0, HNV_SWEEP_JACOBI = 1 } hnv_sweep;
+
+/* How a node picks its hyperedge during coarsening (Section 3.1; the paper
+ * uses "weights or degrees of a hyperedge" when there are no node features
+ * and breaks ties at random). Every policy minimises a 64-bit priority
+ * prio_l(e) over the node's hyperedges, ties going to the smaller ID:
+ *   HASH        prio = mix64(e ^ mix64(seed + l * 0x9E3779B97F4A7C15)),
+ *               mix64 = the SplitMix64 finaliser (default);
+ *   LOW_DEGREE  prio = (min(|e|, 2^24-1) << 40) | (hash >> 24);
+ *   HIGH_WEIGHT prio = ((2^32-1 - float_bits(w_e)) << 32) | (hash >> 32);
+ *   EXPLICIT    prio = explicit_prio[l * m0 + orig(e)], where orig(e) is the
+ *               level-0 ID of hyperedge e (test policy). */
+typedef enum {
+  HNV_ASSIGN_HASH = 0,
+  HNV_ASSIGN_LOW_DEGREE = 1,
+  HNV_ASSIGN_HIGH_WEIGHT = 2,
+  HNV_ASSIGN_EXPLICIT = 3
+} hnv_assign;
+
+typedef struct {
+  int32_t policy;                 /* hnv_assign */
+  int32_t min_nodes;              /* coarsen while n_l > min_nodes ...        */
+  int32_t max_levels;             /* ... and l < max_levels and m_l > 0        */
+  int32_t reserved;
+  uint64_t seed;                  /* hash seed                                 */
+  const uint64_t* explicit_prio;  /* EXPLICIT only: HOST array, max_levels*m0  */
+} hnv_coarsen_params;
+
+typedef struct hnv_graph hnv_graph;
+
+/* ---------------------------------------------------------------------------
+ * hnv_build_incidence -- level 0 of the hierarchy.
+ * The hypergraph H = (V, E, w) (Section 1.1) as hyperedge member lists:
+ * members of hyperedge e are edge_nodes[edge_ptr[e] .. edge_ptr[e+1]).
+ * Builds the star-expansion incidence CSR (hyperedge -> nodes) and CSC
+ * (node -> hyperedges) with ascending, duplicate-free rows, the weighted
+ * node degrees sum_{e ∋ v} w_e (float32, summed in ascending e) and 1/|e|.
+ *   n_nodes, n_edges   : |V| >= 1, |E| >= 0
+ *   edge_ptr [m+1]     : int64, edge_ptr[0] = 0, non-decreasing; every
+ *                        hyperedge non-empty (the paper's hyperedges are
+ *                        non-empty sets) -> else HNV_ERR_INVALID_ARG
+ *   edge_nodes [nnz]   : int32 node IDs in [0, n); repeats are removed;
+ *                        an ID outside -> HNV_ERR_OUT_OF_RANGE
+ *   edge_w [m] or NULL : float32 weights, finite and > 0 (NULL = all 1)
+ *   inputs_on_device   : 1 = the three arrays are device pointers;
+ *                        0 = host pointers (copied by the call)
+ * Synchronises the stream (sizes are read back). On success *out owns the
+ * hierarchy (one level); on failure *out is NULL.
+ * ------------------------------------------------------------------------- */
+int hnv_build_incidence(int32_t n_nodes, int32_t n_edges, const int64_t* edge_ptr,
+                        const int32_t* edge_nodes, const float* edge_w,
+                        int inputs_on_device, hnv_stream_t stream, hnv_graph** out);
+
+/* ---------------------------------------------------------------------------
+ * hnv_coarsen -- Algorithm 1 (Section 3.1), level by level, on the graph's
+ * stream. Per level l: every node v picks c(v) = argmin_{e in N(v)}
+ * (prio_l(e), e); nodes with equal c(v) merge into one coarse node, a node
+ * in no hyperedge stays alone; coarse IDs are the ranks of c(v) (or m_l + v
+ * for a lone node). A hyperedge survives iff its members map to >= 2
+ * distinct coarse nodes; survivors keep their order and weight and get the
+ * sorted distinct images of their members. rep_v[l][v] is v's coarse node;
+ * rep_e[l][e] is e's coarse hyperedge, or -1 - c when e collapsed into
+ * coarse node c. Stops when n_l <= min_nodes, l == max_levels or m_l == 0;
+ * a step that merges nothing is discarded and ends the loop.
+ * Replaces any previous hierarchy above level 0. *n_levels (out) counts
+ * levels including level 0. Synchronises the stream once per level.
+ * ------------------------------------------------------------------------- */
+int hnv_coarsen(hnv_graph* g, const hnv_coarsen_params* p, int32_t* n_levels);
+
+/* Number of levels currently held (>= 1). */
+int hnv_num_levels(const hnv_graph* g, int32_t* n_levels);
+
+/* Sizes of one level. */
+int hnv_level_info(const hnv_graph* g, int level, int32_t* n, int32_t* m, int64_t* nnz);
+
+/* Device pointers of one level's arrays (owned by g, valid until the
+ * hierarchy is rebuilt or freed). Any out pointer may be NULL. rep_v/rep_e
+ * are NULL on the coarsest level. */
+int hnv_get_level_arrays(const hnv_graph* g, int level, const int32_t** e_ptr,
+                         const int32_t** e_nodes, const int32_t** v_ptr,
+                         const int32_t** v_edges, const float** w,
+                         const int32_t** rep_v, const int32_t** rep_e);
+
+/* Which array hnv_copy_level_array() copies, and its element count. */
+typedef enum {
+  HNV_ARR_E_PTR = 0,    /* int32 [m+1]  */
+  HNV_ARR_E_NODES = 1,  /* int32 [nnz]  */
+  HNV_ARR_V_PTR = 2,    /* int32 [n+1]  */
+  HNV_ARR_V_EDGES = 3,  /* int32 [nnz]  */
+  HNV_ARR_W = 4,        /* float [m]    */
+  HNV_ARR_REP_V = 5,    /* int32 [n]    (not on the coarsest level) */
+  HNV_ARR_REP_E = 6,    /* int32 [m]    (not on the coarsest level) */
+  HNV_ARR_DEG_V = 7     /* float [n]    weighted degree sum_{e ∋ v} w_e */
+} hnv_array;
+
+/* Copies one array of a level into dst (device pointer if dst_on_device,
+ * else host) and synchronises the stream. capacity_bytes guards dst. */
+int hnv_copy_level_array(const hnv_graph* g, int level, int which, void* dst,
+                         size_t capacity_bytes, int dst_on_device, hnv_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * hnv_project -- initial embedding of level fine_level from level
+ * fine_level + 1 (Section 3.3: a coarse node's embedding goes to every node
+ * it merged). zf_v[v] = zc_v[rep_v[v]]; zf_e[e] = zc_e[rep_e[e]] if e
+ * survived, else zc_v[c] for the coarse node c it collapsed into (the mean
+ * of its projected members). Bitwise row copies.
+ *   zc_v [n_{l+1} x d], zc_e [m_{l+1} x d] : device, read
+ *   zf_v [n_l x d],     zf_e [m_l x d]     : device, written
+ * ------------------------------------------------------------------------- */
+int hnv_project(const hnv_graph* g, int fine_level, const void* zc_v, const void* zc_e,
+                void* zf_v, void* zf_e, hnv_dtype dt, int d, hnv_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * hnv_refine -- Algorithm 2 (Section 3.3) on one level, in place:
+ * `sweeps` iterations of
+ *   z~_e = (1/|e|) sum_{v in e} z_v,
+ *   z~_v = sum_{e ∋ v} w_e z_e / sum_{e ∋ v} w_e,
+ *   z <- (1 - omega) z + omega z~,
+ * in the given update order; rows with no neighbours are left unchanged.
+ * Sums are float32 in a fixed order (results are deterministic).
+ *   z_v [n_l x d], z_e [m_l x d] : device, read and written
+ *   omega in [0, 1]; sweeps >= 0
+ * ------------------------------------------------------------------------- */
+int hnv_refine(hnv_graph* g, int level, void* z_v, void* z_e, hnv_dtype dt, int d,
+               float omega, int sweeps, hnv_sweep mode, hnv_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * hnv_vcycle -- the refinement half of the V-cycle (Section 3, Fig. 1):
+ * refine the coarsest level L from z_coarsest, then for l = L-1 .. 0
+ * project onto level l and refine it; write level 0's result.
+ *   z_coarsest [(n_L + m_L) x d] : the coarsest level's initial embedding,
+ *                                  node rows first, then hyperedge rows
+ *   z_v_out [n_0 x d], z_e_out [m_0 x d]
+ *   buffers_on_device : 1 = the three buffers are device pointers
+ *                       (asynchronous on the stream);
+ *                       0 = host pointers (copied in and out by the call,
+ *                       which synchronises the stream before returning)
+ * The per-level working buffers are allocated by the call.
+ * ------------------------------------------------------------------------- */
+int hnv_vcycle(hnv_graph* g, const void* z_coarsest, void* z_v_out, void* z_e_out,
+               hnv_dtype dt, int d, float omega, int sweeps_per_level, hnv_sweep mode,
+               int buffers_on_device, hnv_stream_t stream);
+
+/* Releases the hierarchy (stream-ordered on the graph's stream). NULL is a no-op. */
+void hnv_graph_free(hnv_graph* g);
+
+/* ---------------------------------------------------------------------------
+ * Utilities
+ * ------------------------------------------------------------------------- */
+const char* hnv_error_string(int code);
+/* One-line detail of the calling thread's last error ("" if none). */
+const char* hnv_last_error_detail(void);
+
+/* Replaces the device allocator (NULL, NULL restores cudaMallocAsync /
+ * cudaFreeAsync). alloc returns NULL on failure, which the library reports
+ * as HNV_ERR_OOM. Not thread-safe with respect to calls in flight. */
+typedef void* (*hnv_alloc_fn)(size_t bytes, hnv_stream_t stream, void* ctx);
+typedef void (*hnv_free_fn)(void* ptr, hnv_stream_t stream, void* ctx);
+int hnv_set_allocator(hnv_alloc_fn alloc_fn, hnv_free_fn free_fn, void* ctx);
+
+/* Number of kernels this library has launched in the process so far. */
+int64_t hnv_kernel_launch_count(void);
+
+/* Per-phase device timing. When enabled, the library records CUDA events
+ * around each phase's kernels on the launching stream. Phases: */
+typedef enum {
+  HNV_PHASE_BUILD = 0,
+  HNV_PHASE_COARSEN = 1,
+  HNV_PHASE_PROJECT = 2,
+  HNV_PHASE_REFINE_E = 3,   /* hyperedge half-sweeps (gather node rows)   */
+  HNV_PHASE_REFINE_V = 4,   /* node half-sweeps (gather hyperedge rows)   */
+  HNV_PHASE_COUNT = 5
+} hnv_phase;
+int hnv_timing_enable(int enable);
+/* Clears the recorded events. */
+int hnv_timing_reset(void);
+/* Synchronises the recorded events and returns, for one phase, the summed
+ * milliseconds, the number of recorded launches and the summed algorithmic
+ * bytes (compulsory traffic: every input and output array touched once). */
+int hnv_timing_read(int phase, double* total_ms, int64_t* launches, double* alg_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HNV_H_ */

@@ -1,0 +1,312 @@
+"""GB300-native HyperNetVec V-cycle: the Python binding of ``libhnv.so``.
+
+Argument marshalling only: every step of coarsening, projection and
+refinement runs in the library's CUDA kernels. PyTorch supplies device
+memory (tensors) and streams. Importing this package does not load the
+library; the first call does, and raises ``HNVLibraryMissing`` when the
+in-tree ``libhnv.so`` has not been built -- there is no CPU fallback.
+
+The functions named like the C entry points (``hnv_build_incidence``,
+``hnv_coarsen``, ``hnv_project``, ``hnv_refine``, ``hnv_vcycle``) take the
+same arguments as in ``include/hnv.h`` with tensors/arrays in place of raw
+pointers; ``Graph`` wraps them for convenience.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Tuple
+
+import numpy as np
+
+__all__ = [
+    "HNVError", "HNVLibraryMissing", "lib", "library_path",
+    "ASSIGN_HASH", "ASSIGN_LOW_DEGREE", "ASSIGN_HIGH_WEIGHT", "ASSIGN_EXPLICIT",
+    "SWEEP_TWO_PHASE", "SWEEP_JACOBI", "F32", "BF16",
+    "ARR_E_PTR", "ARR_E_NODES", "ARR_V_PTR", "ARR_V_EDGES", "ARR_W", "ARR_REP_V",
+    "ARR_REP_E", "ARR_DEG_V",
+    "PHASE_BUILD", "PHASE_COARSEN", "PHASE_PROJECT", "PHASE_REFINE_E", "PHASE_REFINE_V",
+    "Graph", "hnv_build_incidence", "hnv_coarsen", "hnv_project", "hnv_refine",
+    "hnv_vcycle", "kernel_launch_count", "timing_enable", "timing_reset", "timing_read",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+library_path = os.path.join(_HERE, "libhnv.so")
+
+# enums of include/hnv.h
+ASSIGN_HASH, ASSIGN_LOW_DEGREE, ASSIGN_HIGH_WEIGHT, ASSIGN_EXPLICIT = 0, 1, 2, 3
+SWEEP_TWO_PHASE, SWEEP_JACOBI = 0, 1
+F32, BF16 = 0, 1
+(ARR_E_PTR, ARR_E_NODES, ARR_V_PTR, ARR_V_EDGES, ARR_W, ARR_REP_V, ARR_REP_E,
+ ARR_DEG_V) = range(8)
+PHASE_BUILD, PHASE_COARSEN, PHASE_PROJECT, PHASE_REFINE_E, PHASE_REFINE_V = range(5)
+
+ERR_NAMES = {0: "HNV_OK", -1: "HNV_ERR_INVALID_ARG", -2: "HNV_ERR_OUT_OF_RANGE",
+             -3: "HNV_ERR_TOO_LARGE", -4: "HNV_ERR_OOM", -5: "HNV_ERR_CUDA",
+             -6: "HNV_ERR_TIMEOUT", -7: "HNV_ERR_UNSUPPORTED_D", -8: "HNV_ERR_STATE"}
+
+
+class HNVError(RuntimeError):
+    """A non-zero status returned by libhnv.so."""
+
+    def __init__(self, code: int, where: str, detail: str):
+        self.code = code
+        super().__init__("%s returned %s (%d): %s" % (where, ERR_NAMES.get(code, "?"), code, detail))
+
+
+class HNVLibraryMissing(ImportError):
+    pass
+
+
+class CoarsenParams(ctypes.Structure):
+    _fields_ = [("policy", ctypes.c_int32), ("min_nodes", ctypes.c_int32),
+                ("max_levels", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("explicit_prio", ctypes.c_void_p)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def _declare(L):
+    i32, i64, f32, sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_size_t
+    sig = {
+        "hnv_build_incidence": (ctypes.c_int, [i32, i32, _P, _P, _P, ctypes.c_int, _P, ctypes.POINTER(_P)]),
+        "hnv_coarsen": (ctypes.c_int, [_P, ctypes.POINTER(CoarsenParams), ctypes.POINTER(i32)]),
+        "hnv_num_levels": (ctypes.c_int, [_P, ctypes.POINTER(i32)]),
+        "hnv_level_info": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i64)]),
+        "hnv_get_level_arrays": (ctypes.c_int, [_P, ctypes.c_int] + [ctypes.POINTER(_P)] * 7),
+        "hnv_copy_level_array": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, sz, ctypes.c_int, _P]),
+        "hnv_project": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, ctypes.c_int, ctypes.c_int, _P]),
+        "hnv_refine": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_int, f32, ctypes.c_int, ctypes.c_int, _P]),
+        "hnv_vcycle": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_int, f32, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
+        "hnv_graph_free": (None, [_P]),
+        "hnv_error_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "hnv_last_error_detail": (ctypes.c_char_p, []),
+        "hnv_set_allocator": (ctypes.c_int, [_P, _P, _P]),
+        "hnv_kernel_launch_count": (i64, []),
+        "hnv_timing_enable": (ctypes.c_int, [ctypes.c_int]),
+        "hnv_timing_reset": (ctypes.c_int, []),
+        "hnv_timing_read": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+def lib():
+    """The loaded library (loads it on first use; raises if it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(library_path):
+            raise HNVLibraryMissing(
+                "libhnv.so is not built (run paper_2103_09660_gb300/build.py); "
+                "there is no CPU fallback")
+        _lib = _declare(ctypes.CDLL(library_path))
+    return _lib
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise HNVError(rc, where, lib().hnv_last_error_detail().decode(errors="replace"))
+
+
+def _stream_handle(stream) -> Optional[int]:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def _dev_ptr(t, dtype, name: str, rows: Optional[int] = None, d: Optional[int] = None) -> int:
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError("%s must be a contiguous %s tensor" % (name, dtype))
+    if rows is not None and d is not None and tuple(t.shape) != (rows, d):
+        raise ValueError("%s must have shape (%d, %d), got %s" % (name, rows, d, tuple(t.shape)))
+    return t.data_ptr()
+
+
+# ---------------------------------------------------------------------------
+# Entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------
+
+def hnv_build_incidence(n: int, m: int, edge_ptr, edge_nodes, edge_w=None, stream=None) -> int:
+    """Returns the opaque graph handle. Arrays are numpy (host) or CUDA
+    tensors (device): int64 edge_ptr[m+1], int32 edge_nodes[nnz], float32
+    edge_w[m] or None."""
+    import torch
+    on_dev = isinstance(edge_ptr, torch.Tensor)
+    keep = []
+    if on_dev:
+        p = _dev_ptr(edge_ptr, torch.int64, "edge_ptr")
+        q = _dev_ptr(edge_nodes, torch.int32, "edge_nodes")
+        w = _dev_ptr(edge_w, torch.float32, "edge_w") if edge_w is not None else None
+    else:
+        a = np.ascontiguousarray(edge_ptr, dtype=np.int64)
+        b = np.ascontiguousarray(edge_nodes, dtype=np.int32)
+        c = np.ascontiguousarray(edge_w, dtype=np.float32) if edge_w is not None else None
+        keep = [a, b, c]
+        p, q = a.ctypes.data, (b.ctypes.data if b.size else None)
+        w = c.ctypes.data if c is not None else None
+    g = _P()
+    rc = lib().hnv_build_incidence(int(n), int(m), p, q, w, 1 if on_dev else 0,
+                                   _stream_handle(stream), ctypes.byref(g))
+    del keep
+    _check(rc, "hnv_build_incidence")
+    return g.value
+
+
+def hnv_coarsen(g: int, policy: int = ASSIGN_HASH, seed: int = 0, min_nodes: int = 200,
+                max_levels: int = 32, explicit_prio=None) -> int:
+    tab = None
+    if explicit_prio is not None:
+        tab = np.ascontiguousarray(explicit_prio, dtype=np.uint64)
+    prm = CoarsenParams(policy, min_nodes, max_levels, 0, seed & ((1 << 64) - 1),
+                        tab.ctypes.data if tab is not None else None)
+    out = ctypes.c_int32()
+    _check(lib().hnv_coarsen(g, ctypes.byref(prm), ctypes.byref(out)), "hnv_coarsen")
+    return out.value
+
+
+def hnv_project(g: int, fine_level: int, zc_v, zc_e, zf_v, zf_e, stream=None):
+    import torch
+    d = zf_v.shape[1] if zf_v.dim() == 2 else zc_v.shape[1]
+    _check(lib().hnv_project(g, fine_level, _dev_ptr(zc_v, torch.float32, "zc_v"),
+                             _dev_ptr(zc_e, torch.float32, "zc_e"),
+                             _dev_ptr(zf_v, torch.float32, "zf_v"),
+                             _dev_ptr(zf_e, torch.float32, "zf_e"), F32, int(d),
+                             _stream_handle(stream)), "hnv_project")
+
+
+def hnv_refine(g: int, level: int, z_v, z_e, omega: float = 0.5, sweeps: int = 10,
+               mode: int = SWEEP_TWO_PHASE, stream=None):
+    import torch
+    d = z_v.shape[1]
+    _check(lib().hnv_refine(g, level, _dev_ptr(z_v, torch.float32, "z_v"),
+                            _dev_ptr(z_e, torch.float32, "z_e"), F32, int(d), float(omega),
+                            int(sweeps), int(mode), _stream_handle(stream)), "hnv_refine")
+
+
+def hnv_vcycle(g: int, z_coarsest, z_v_out, z_e_out, omega: float = 0.5, sweeps: int = 10,
+               mode: int = SWEEP_TWO_PHASE, stream=None):
+    """Device tensors (asynchronous) or numpy arrays (host; synchronous)."""
+    import torch
+    if isinstance(z_coarsest, torch.Tensor):
+        d = z_coarsest.shape[1]
+        args = (_dev_ptr(z_coarsest, torch.float32, "z_coarsest"),
+                _dev_ptr(z_v_out, torch.float32, "z_v_out"),
+                _dev_ptr(z_e_out, torch.float32, "z_e_out"))
+        on_dev = 1
+    else:
+        for a, nm in ((z_coarsest, "z_coarsest"), (z_v_out, "z_v_out"), (z_e_out, "z_e_out")):
+            if a.dtype != np.float32 or not a.flags.c_contiguous:
+                raise TypeError("%s must be a C-contiguous float32 array" % nm)
+        d = z_coarsest.shape[1]
+        args = (z_coarsest.ctypes.data, z_v_out.ctypes.data, z_e_out.ctypes.data)
+        on_dev = 0
+    _check(lib().hnv_vcycle(g, *args, F32, int(d), float(omega), int(sweeps), int(mode), on_dev,
+                            _stream_handle(stream)), "hnv_vcycle")
+
+
+def kernel_launch_count() -> int:
+    return int(lib().hnv_kernel_launch_count())
+
+
+def timing_enable(on: bool = True):
+    _check(lib().hnv_timing_enable(1 if on else 0), "hnv_timing_enable")
+
+
+def timing_reset():
+    _check(lib().hnv_timing_reset(), "hnv_timing_reset")
+
+
+def timing_read(phase: int) -> Tuple[float, int, float]:
+    """(total ms, launches, algorithmic bytes) recorded for one phase."""
+    ms = ctypes.c_double()
+    cnt = ctypes.c_int64()
+    by = ctypes.c_double()
+    _check(lib().hnv_timing_read(phase, ctypes.byref(ms), ctypes.byref(cnt), ctypes.byref(by)),
+           "hnv_timing_read")
+    return ms.value, cnt.value, by.value
+
+
+# ---------------------------------------------------------------------------
+# Convenience wrapper
+# ---------------------------------------------------------------------------
+
+class Graph:
+    """An owned hierarchy (``hnv_graph``) built from a hypergraph."""
+
+    def __init__(self, n: int, m: int, edge_ptr, edge_nodes, edge_w=None, stream=None):
+        import torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.handle = hnv_build_incidence(n, m, edge_ptr, edge_nodes, edge_w, self.stream)
+
+    @classmethod
+    def from_hypergraph(cls, hg, on_device: bool = False, stream=None) -> "Graph":
+        if on_device:
+            import torch
+            return cls(hg.n, hg.m, torch.from_numpy(hg.edge_ptr).cuda(),
+                       torch.from_numpy(hg.edge_nodes).cuda(),
+                       torch.from_numpy(hg.weights).cuda(), stream)
+        return cls(hg.n, hg.m, hg.edge_ptr, hg.edge_nodes, hg.weights, stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().hnv_graph_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def coarsen(self, **kw) -> int:
+        return hnv_coarsen(self.handle, **kw)
+
+    @property
+    def num_levels(self) -> int:
+        out = ctypes.c_int32()
+        _check(lib().hnv_num_levels(self.handle, ctypes.byref(out)), "hnv_num_levels")
+        return out.value
+
+    def level_info(self, level: int) -> Tuple[int, int, int]:
+        n, m, nnz = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        _check(lib().hnv_level_info(self.handle, level, ctypes.byref(n), ctypes.byref(m),
+                                    ctypes.byref(nnz)), "hnv_level_info")
+        return n.value, m.value, nnz.value
+
+    def level_array(self, level: int, which: int) -> np.ndarray:
+        """Host copy of one array of a level."""
+        n, m, nnz = self.level_info(level)
+        count = {ARR_E_PTR: m + 1, ARR_E_NODES: nnz, ARR_V_PTR: n + 1, ARR_V_EDGES: nnz,
+                 ARR_W: m, ARR_REP_V: n, ARR_REP_E: m, ARR_DEG_V: n}[which]
+        dt = np.float32 if which in (ARR_W, ARR_DEG_V) else np.int32
+        out = np.empty(count, dtype=dt)
+        _check(lib().hnv_copy_level_array(self.handle, level, which,
+                                          out.ctypes.data if count else None, out.nbytes, 0,
+                                          _stream_handle(self.stream)),
+               "hnv_copy_level_array")
+        return out
+
+    def refine(self, level: int, z_v, z_e, omega=0.5, sweeps=10, mode=SWEEP_TWO_PHASE):
+        hnv_refine(self.handle, level, z_v, z_e, omega, sweeps, mode, self.stream)
+
+    def project(self, fine_level: int, zc_v, zc_e, zf_v, zf_e):
+        hnv_project(self.handle, fine_level, zc_v, zc_e, zf_v, zf_e, self.stream)
+
+    def vcycle(self, z_coarsest, z_v_out, z_e_out, omega=0.5, sweeps=10, mode=SWEEP_TWO_PHASE):
+        hnv_vcycle(self.handle, z_coarsest, z_v_out, z_e_out, omega, sweeps, mode, self.stream)

@@ -1,0 +1,268 @@
+// One coarsening step (Algorithm 1, Section 3.1), integer only and
+// bit-exact: every node picks a hyperedge, nodes that picked the same
+// hyperedge merge into one coarse node, hyperedges whose members all merged
+// into one coarse node are removed, the rest connect the coarse nodes of
+// their members.
+#include "hnv_internal.cuh"
+
+namespace hnv {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;  // SplitMix64 increment
+
+// SplitMix64 finaliser (Steele, Lea & Flood, OOPSLA 2014).
+__host__ __device__ inline uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// prio_l(e) for the policies of hnv_assign (see hnv.h).
+__global__ void priority_kernel(int32_t m, int32_t policy, uint64_t salt,
+                                const int32_t* __restrict__ e_ptr, const float* __restrict__ w,
+                                const int32_t* __restrict__ orig_e,
+                                const uint64_t* __restrict__ explicit_tab,
+                                uint64_t* __restrict__ prio) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t h = mix64((uint64_t)e ^ salt);
+    uint64_t p = h;
+    if (policy == HNV_ASSIGN_LOW_DEGREE) {
+      uint64_t sz = (uint64_t)(e_ptr[e + 1] - e_ptr[e]);
+      if (sz > 0xFFFFFFull) sz = 0xFFFFFFull;
+      p = (sz << 40) | (h >> 24);
+    } else if (policy == HNV_ASSIGN_HIGH_WEIGHT) {
+      const uint64_t bits = (uint64_t)__float_as_uint(w[e]);
+      p = ((0xFFFFFFFFull - bits) << 32) | (h >> 32);
+    } else if (policy == HNV_ASSIGN_EXPLICIT) {
+      p = explicit_tab[orig_e[e]];
+    }
+    prio[e] = p;
+  }
+}
+
+// c(v) = argmin_{e in N(v)} (prio(e), e), or -1; warp per node, lanes stride
+// the CSC row, then a lexicographic min over the warp.
+__global__ void assign_kernel(int32_t n, const int32_t* __restrict__ v_ptr,
+                              const int32_t* __restrict__ v_edges,
+                              const uint64_t* __restrict__ prio, int32_t* __restrict__ c) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t v = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); v < n;
+       v += warps) {
+    const int64_t b = v_ptr[v], end = v_ptr[v + 1];
+    uint64_t bp = ~0ull;
+    int32_t be = 0x7fffffff;
+    for (int64_t k = b + lane; k < end; k += 32) {
+      const int32_t e = v_edges[k];
+      const uint64_t p = prio[e];
+      if (p < bp || (p == bp && e < be)) {
+        bp = p;
+        be = e;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const uint64_t op = __shfl_xor_sync(FULL, bp, o);
+      const int32_t oe = __shfl_xor_sync(FULL, be, o);
+      if (op < bp || (op == bp && oe < be)) {
+        bp = op;
+        be = oe;
+      }
+    }
+    if (lane == 0) c[v] = (end > b) ? be : -1;
+  }
+}
+
+// key(v) = c(v) or m + v; flags[key] = 1 (all writers store the same value).
+__global__ void mark_keys_kernel(int32_t n, int32_t m, const int32_t* __restrict__ c,
+                                 int32_t* __restrict__ flags) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t cv = c[v];
+    flags[cv >= 0 ? (int64_t)cv : (int64_t)m + v] = 1;
+  }
+}
+
+__global__ void rep_v_kernel(int32_t n, int32_t m, const int32_t* __restrict__ c,
+                             const int32_t* __restrict__ rank, int32_t* __restrict__ rep_v) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t cv = c[v];
+    rep_v[v] = rank[cv >= 0 ? (int64_t)cv : (int64_t)m + v];
+  }
+}
+
+// key = (e << 32) | rep_v[member], warp per hyperedge.
+__global__ void pack_image_keys(int32_t m, const int32_t* __restrict__ e_ptr,
+                                const int32_t* __restrict__ e_nodes,
+                                const int32_t* __restrict__ rep_v, uint64_t* __restrict__ keys) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); e < m;
+       e += warps) {
+    const int64_t b = e_ptr[e], end = e_ptr[e + 1];
+    for (int64_t k = b + lane; k < end; k += 32)
+      keys[k] = ((uint64_t)(uint32_t)e << 32) | (uint32_t)rep_v[e_nodes[k]];
+  }
+}
+
+__global__ void image_first_kernel(const uint64_t* __restrict__ keys, int64_t n,
+                                   int32_t* __restrict__ first, int32_t* __restrict__ img_size) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const bool f = (k == 0 || keys[k] != keys[k - 1]);
+    first[k] = f ? 1 : 0;
+    if (f) atomicAdd(&img_size[(uint32_t)(keys[k] >> 32)], 1);
+  }
+}
+
+__global__ void keep_kernel(int32_t m, const int32_t* __restrict__ img_size,
+                            int32_t* __restrict__ keep) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x)
+    keep[e] = img_size[e] >= 2 ? 1 : 0;
+}
+
+// Entries of surviving hyperedges: flag2 = first && keep[row]. Removed
+// hyperedges (image of size 1) record -1 - c in rep_e.
+__global__ void survivor_entries(const uint64_t* __restrict__ keys, int64_t n,
+                                 const int32_t* __restrict__ first, const int32_t* __restrict__ keep,
+                                 int32_t* __restrict__ flag2, int32_t* __restrict__ rep_e) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t key = keys[k];
+    const uint32_t e = (uint32_t)(key >> 32);
+    const int32_t f = first[k];
+    const int32_t kp = keep[e];
+    flag2[k] = (f && kp) ? 1 : 0;
+    if (f && !kp) rep_e[e] = -1 - (int32_t)(uint32_t)key;
+  }
+}
+
+__global__ void scatter_survivors(const uint64_t* __restrict__ keys, int64_t n,
+                                  const int32_t* __restrict__ flag2, const int32_t* __restrict__ pos,
+                                  int32_t* __restrict__ e_nodes2) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    if (flag2[k]) e_nodes2[pos[k]] = (int32_t)(uint32_t)keys[k];
+}
+
+// Per fine hyperedge: survivors get their new ID in rep_e and carry their
+// size, weight and level-0 ID to the coarse level.
+__global__ void survivor_rows(int32_t m, const int32_t* __restrict__ keep,
+                              const int32_t* __restrict__ new_id,
+                              const int32_t* __restrict__ img_size, const float* __restrict__ w,
+                              const int32_t* __restrict__ orig_e, int32_t* __restrict__ rep_e,
+                              int32_t* __restrict__ size2, float* __restrict__ w2,
+                              int32_t* __restrict__ orig2) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    if (!keep[e]) continue;
+    const int32_t r = new_id[e];
+    rep_e[e] = r;
+    size2[r] = img_size[e];
+    w2[r] = w[e];
+    orig2[r] = orig_e[e];
+  }
+}
+
+}  // namespace
+
+int coarsen_step(hnv_graph* g, int level, const hnv_coarsen_params* p,
+                 const uint64_t* d_explicit, Level* fine, Level* coarse) {
+  cudaStream_t s = g->stream;
+  const int32_t n = fine->n, m = fine->m;
+  const int64_t nnz = fine->nnz;
+  TempPool pool(s);
+
+  // 1. AssignHyperedge for every node
+  uint64_t* prio = nullptr;
+  int32_t* c = nullptr;
+  HNV_CHECK(pool.get(&prio, (size_t)m));
+  HNV_CHECK(pool.get(&c, (size_t)n));
+  const uint64_t salt = mix64(p->seed + (uint64_t)level * kGamma);
+  HNV_CHECK(launch("priority", priority_kernel, grid_for(m, 256), 256, 0, s, m, p->policy, salt,
+                   (const int32_t*)fine->e_ptr, (const float*)fine->w,
+                   (const int32_t*)fine->orig_e, d_explicit, prio));
+  HNV_CHECK(launch("assign", assign_kernel, grid_for((int64_t)n * 32, 256), 256, 0, s, n,
+                   (const int32_t*)fine->v_ptr, (const int32_t*)fine->v_edges,
+                   (const uint64_t*)prio, c));
+
+  // 2. Merge: coarse IDs are the ranks of the keys c(v) / m + v
+  int32_t* rank = nullptr;
+  const int64_t nkeys = (int64_t)m + n;
+  HNV_CHECK(pool.get(&rank, (size_t)nkeys));
+  HNV_CUDA(cudaMemsetAsync(rank, 0, sizeof(int32_t) * nkeys, s));
+  HNV_CHECK(launch("mark_keys", mark_keys_kernel, grid_for(n, 256), 256, 0, s, n, m,
+                   (const int32_t*)c, rank));
+  HNV_CHECK(exclusive_scan_i32(rank, rank, nkeys, g->d_buf, s));
+  int32_t n2 = 0;
+  HNV_CHECK(read_ints(g, g->d_buf, 1, &n2, s));
+  HNV_CHECK(level_alloc(fine, (void**)&fine->rep_v, sizeof(int32_t) * (size_t)n, s));
+  HNV_CHECK(level_alloc(fine, (void**)&fine->rep_e, sizeof(int32_t) * (size_t)m, s));
+  HNV_CHECK(launch("rep_v", rep_v_kernel, grid_for(n, 256), 256, 0, s, n, m, (const int32_t*)c,
+                   (const int32_t*)rank, fine->rep_v));
+
+  // 3. Images of the hyperedges: sorted distinct rep_v of the members
+  uint64_t *k0 = nullptr, *k1 = nullptr, *sorted = nullptr;
+  int32_t *first = nullptr, *img_size = nullptr, *keep = nullptr, *new_id = nullptr;
+  HNV_CHECK(pool.get(&k0, (size_t)nnz));
+  HNV_CHECK(pool.get(&k1, (size_t)nnz));
+  HNV_CHECK(launch("pack_image_keys", pack_image_keys, grid_for((int64_t)m * 32, 256), 256, 0, s,
+                   m, (const int32_t*)fine->e_ptr, (const int32_t*)fine->e_nodes,
+                   (const int32_t*)fine->rep_v, k0));
+  int shifts[16];
+  const int np = radix_shifts(bits_for_count(n2), bits_for_count(m), shifts);
+  HNV_CHECK(radix_sort_u64(k0, k1, nnz, shifts, np, s, &sorted));
+  HNV_CHECK(pool.get(&first, (size_t)nnz));
+  HNV_CHECK(pool.get(&img_size, (size_t)m + 1));
+  HNV_CHECK(pool.get(&keep, (size_t)m + 1));
+  HNV_CHECK(pool.get(&new_id, (size_t)m + 1));
+  HNV_CUDA(cudaMemsetAsync(img_size, 0, sizeof(int32_t) * ((size_t)m + 1), s));
+  HNV_CHECK(launch("image_first", image_first_kernel, grid_for(nnz, 256), 256, 0, s,
+                   (const uint64_t*)sorted, nnz, first, img_size));
+
+  // 4. addHedge: survivors have >= 2 distinct coarse members
+  HNV_CHECK(launch("keep", keep_kernel, grid_for(m, 256), 256, 0, s, m,
+                   (const int32_t*)img_size, keep));
+  HNV_CHECK(exclusive_scan_i32(keep, new_id, m, g->d_buf, s));
+  int32_t* flag2 = nullptr;
+  int32_t* pos = nullptr;
+  HNV_CHECK(pool.get(&flag2, (size_t)nnz));
+  HNV_CHECK(pool.get(&pos, (size_t)nnz));
+  HNV_CHECK(launch("survivor_entries", survivor_entries, grid_for(nnz, 256), 256, 0, s,
+                   (const uint64_t*)sorted, nnz, (const int32_t*)first, (const int32_t*)keep,
+                   flag2, fine->rep_e));
+  HNV_CHECK(exclusive_scan_i32(flag2, pos, nnz, g->d_buf + 1, s));
+  int32_t h[2];
+  HNV_CHECK(read_ints(g, g->d_buf, 2, h, s));
+  const int32_t m2 = h[0];
+  const int32_t nnz2 = h[1];
+
+  // 5. addNode/addEdge: the coarse level's CSR, weights and level-0 IDs
+  *coarse = Level();
+  coarse->n = n2;
+  coarse->m = m2;
+  coarse->nnz = nnz2;
+  int32_t* size2 = nullptr;
+  HNV_CHECK(pool.get(&size2, (size_t)m2 + 1));
+  HNV_CHECK(level_alloc(coarse, (void**)&coarse->e_ptr, sizeof(int32_t) * ((size_t)m2 + 1), s));
+  HNV_CHECK(level_alloc(coarse, (void**)&coarse->e_nodes, sizeof(int32_t) * (size_t)nnz2, s));
+  HNV_CHECK(level_alloc(coarse, (void**)&coarse->w, sizeof(float) * (size_t)m2, s));
+  HNV_CHECK(level_alloc(coarse, (void**)&coarse->orig_e, sizeof(int32_t) * (size_t)m2, s));
+  HNV_CHECK(launch("scatter_survivors", scatter_survivors, grid_for(nnz, 256), 256, 0, s,
+                   (const uint64_t*)sorted, nnz, (const int32_t*)flag2, (const int32_t*)pos,
+                   coarse->e_nodes));
+  HNV_CUDA(cudaMemsetAsync(size2, 0, sizeof(int32_t) * ((size_t)m2 + 1), s));
+  HNV_CHECK(launch("survivor_rows", survivor_rows, grid_for(m, 256), 256, 0, s, m,
+                   (const int32_t*)keep, (const int32_t*)new_id, (const int32_t*)img_size,
+                   (const float*)fine->w, (const int32_t*)fine->orig_e, fine->rep_e, size2,
+                   coarse->w, coarse->orig_e));
+  HNV_CHECK(exclusive_scan_i32(size2, coarse->e_ptr, (int64_t)m2 + 1, nullptr, s));
+  return HNV_OK;
+}
+
+}  // namespace hnv

@@ -1,0 +1,228 @@
+// Internal declarations shared by the translation units of libhnv.so.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <utility>
+#include <vector>
+
+#include "hnv.h"
+
+namespace hnv {
+
+// ---------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------
+
+// Records a one-line message for hnv_last_error_detail() (thread-local).
+void set_error_detail(const char* fmt, ...);
+void clear_error_detail();
+int cuda_status(cudaError_t e, const char* what);
+
+#define HNV_FAIL(code, ...)                 \
+  do {                                      \
+    ::hnv::set_error_detail(__VA_ARGS__);   \
+    return (code);                          \
+  } while (0)
+
+#define HNV_CHECK(expr)                     \
+  do {                                      \
+    int hnv_s_ = (expr);                    \
+    if (hnv_s_ != HNV_OK) return hnv_s_;    \
+  } while (0)
+
+#define HNV_CUDA(call)                                             \
+  do {                                                             \
+    cudaError_t hnv_e_ = (call);                                   \
+    if (hnv_e_ != cudaSuccess) return ::hnv::cuda_status(hnv_e_, #call); \
+  } while (0)
+
+// Bits of the per-graph device error word (set with atomicOr by kernels that
+// validate input; read back by the host after a synchronising step).
+enum : int32_t {
+  ERRBIT_NODE_RANGE = 1,    // an input node ID outside [0, n)
+  ERRBIT_EMPTY_EDGE = 2,    // an input hyperedge with no members
+  ERRBIT_BAD_WEIGHT = 4,    // a weight that is not finite and > 0
+  ERRBIT_BAD_PTR = 8        // edge_ptr not starting at 0 / decreasing
+};
+
+// ---------------------------------------------------------------------------
+// Kernel launches
+// ---------------------------------------------------------------------------
+
+void note_launch();
+int num_sms();
+
+// Launches kernel<<<grid, block, smem, s>>>(args...) and counts it. A launch
+// with no blocks is skipped.
+template <typename... KArgs, typename... Args>
+int launch(const char* name, void (*kernel)(KArgs...), unsigned grid, unsigned block,
+           size_t smem, cudaStream_t s, Args&&... args) {
+  if (grid == 0) return HNV_OK;
+  kernel<<<grid, block, smem, s>>>(static_cast<KArgs>(std::forward<Args>(args))...);
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e, name);
+  return HNV_OK;
+}
+
+// Blocks for a grid-stride loop over `items` with `per_block` items per
+// block, capped at `waves` blocks per SM.
+unsigned grid_for(int64_t items, int64_t per_block, int waves = 8);
+
+// ---------------------------------------------------------------------------
+// Device memory (stream-ordered; replaceable through hnv_set_allocator)
+// ---------------------------------------------------------------------------
+
+int dev_alloc(void** p, size_t bytes, cudaStream_t s);
+void dev_free(void* p, cudaStream_t s);
+
+// Temporary device buffers released (stream-ordered) when the pool dies.
+class TempPool {
+ public:
+  explicit TempPool(cudaStream_t s) : s_(s) {}
+  ~TempPool() {
+    for (void* p : ptrs_) dev_free(p, s_);
+  }
+  TempPool(const TempPool&) = delete;
+  TempPool& operator=(const TempPool&) = delete;
+  template <typename T>
+  int get(T** out, size_t count) {
+    void* p = nullptr;
+    HNV_CHECK(dev_alloc(&p, (count ? count : 1) * sizeof(T), s_));
+    ptrs_.push_back(p);
+    *out = static_cast<T*>(p);
+    return HNV_OK;
+  }
+
+ private:
+  cudaStream_t s_;
+  std::vector<void*> ptrs_;
+};
+
+// ---------------------------------------------------------------------------
+// Phase timing (CUDA events on the launching stream)
+// ---------------------------------------------------------------------------
+
+bool timing_on();
+// Records the start event of a phase; returns an opaque slot or -1.
+int timing_begin(int phase, cudaStream_t s, double alg_bytes);
+void timing_end(int slot, cudaStream_t s);
+
+struct PhaseScope {
+  int slot;
+  cudaStream_t s;
+  PhaseScope(int phase, cudaStream_t st, double bytes) : slot(-1), s(st) {
+    if (timing_on()) slot = timing_begin(phase, st, bytes);
+  }
+  ~PhaseScope() {
+    if (slot >= 0) timing_end(slot, s);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Primitives (prims.cu)
+// ---------------------------------------------------------------------------
+
+// out[i] = sum_{j<i} in[i]; in == out allowed. If total != nullptr the sum of
+// all n inputs is written to *total (device). n may be 0.
+int exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, int32_t* total,
+                       cudaStream_t s);
+
+// Stable LSD radix sort of 64-bit keys, one pass of 8 bits per entry of
+// `shifts` (digit = (key >> shift) & 255), ping-ponging between keys and alt.
+// *result receives whichever buffer holds the sorted keys.
+int radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, const int* shifts,
+                   int npasses, cudaStream_t s, uint64_t** result);
+
+// Shifts for the passes that sort the low `low_bits` bits, then bits
+// [32, 32 + high_bits). Returns the number of passes.
+int radix_shifts(int low_bits, int high_bits, int* shifts);
+
+// Number of bits needed to hold values in [0, count).
+int bits_for_count(int64_t count);
+
+int fill_i32(int32_t* p, int32_t value, int64_t n, cudaStream_t s);
+
+// CSC (transpose) of a CSR with ascending rows: col_ptr[n_cols+1] and
+// col_rows[nnz] with ascending entries per column.
+int transpose_csr(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t* row_ptr,
+                  const int32_t* cols, int32_t* col_ptr, int32_t* col_rows, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// The hierarchy
+// ---------------------------------------------------------------------------
+
+// Work plan of one half-sweep: rows longer than `T` incidences are split into
+// chunks of at most T consecutive incidences whose partial sums are reduced
+// in chunk order by a second kernel.
+struct SplitPlan {
+  int32_t T = 0;
+  int32_t n_long = 0;
+  int32_t n_chunks = 0;
+  int32_t* long_rows = nullptr;   // [n_long]
+  int32_t* chunk_ptr = nullptr;   // [n_long + 1]
+  int2* chunk_range = nullptr;    // [n_chunks] (begin, end) incidence ranges
+};
+
+struct Level {
+  int32_t n = 0, m = 0;
+  int64_t nnz = 0;
+  int32_t* e_ptr = nullptr;      // [m+1]
+  int32_t* e_nodes = nullptr;    // [nnz]
+  int32_t* v_ptr = nullptr;      // [n+1]
+  int32_t* v_edges = nullptr;    // [nnz]
+  float* w = nullptr;            // [m]
+  float* v_w = nullptr;          // [nnz] w of each CSC entry
+  float* deg_v = nullptr;        // [n] sum_{e ∋ v} w_e
+  float* inv_deg_v = nullptr;    // [n] 1/deg_v (0 if no hyperedge)
+  float* inv_size_e = nullptr;   // [m] 1/|e|
+  int32_t* orig_e = nullptr;     // [m] level-0 ID
+  int32_t* rep_v = nullptr;      // [n] -> level+1 (null on the coarsest)
+  int32_t* rep_e = nullptr;      // [m] -> level+1 or -1-c
+  SplitPlan planE, planV;
+  std::vector<void*> owned;      // every device allocation of this level
+};
+
+}  // namespace hnv
+
+struct hnv_graph {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<hnv::Level> levels;
+  int32_t* d_err = nullptr;      // device error word
+  int32_t* h_buf = nullptr;      // pinned host scratch (64 ints)
+  int32_t* d_buf = nullptr;      // device scratch (64 ints)
+  float* partials = nullptr;     // split-row partial sums
+  size_t partials_bytes = 0;
+  float* jacobi_tmp = nullptr;   // Jacobi: next hyperedge rows
+  size_t jacobi_bytes = 0;
+};
+
+namespace hnv {
+
+// incidence.cu: level-0 construction, derived arrays and split plans.
+int build_level0(hnv_graph* g, int32_t n, int32_t m, const int64_t* d_edge_ptr,
+                 const int32_t* d_edge_nodes, const float* d_w, Level* out);
+int finish_level(hnv_graph* g, Level* lv);   // derived arrays + plans
+void free_level(Level* lv, cudaStream_t s);
+int level_alloc(Level* lv, void** p, size_t bytes, cudaStream_t s);
+
+// coarsen.cu: one step of Algorithm 1.
+int coarsen_step(hnv_graph* g, int level, const hnv_coarsen_params* p, const uint64_t* d_explicit,
+                 Level* fine, Level* coarse);
+
+// refine.cu
+int refine_level(hnv_graph* g, int level, float* z_v, float* z_e, int d, float omega,
+                 int sweeps, int mode, cudaStream_t s);
+int project_level(const hnv_graph* g, int fine_level, const float* zc_v, const float* zc_e,
+                  float* zf_v, float* zf_e, int d, cudaStream_t s);
+
+// Reads the device error word (synchronising s) and clears it.
+int read_and_clear_err(hnv_graph* g, cudaStream_t s, int32_t* bits);
+// Copies `count` device ints into the graph's pinned buffer and synchronises.
+int read_ints(hnv_graph* g, const int32_t* d_src, int count, int32_t* host_out, cudaStream_t s);
+
+}  // namespace hnv

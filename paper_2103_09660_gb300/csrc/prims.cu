@@ -1,0 +1,288 @@
+// Integer primitives for the coarsening path: exclusive scan, a stable LSD
+// radix sort of 64-bit keys and the CSR transpose built on it. All integer,
+// all deterministic (atomics only count into integer histograms).
+#include "hnv_internal.cuh"
+
+namespace hnv {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of int32 (three kernels per level of recursion)
+// ---------------------------------------------------------------------------
+
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+// Exclusive scan of one value per thread over a 256-thread block. Returns the
+// exclusive prefix; *block_total receives the block's sum.
+__device__ int32_t block_exclusive_scan(int32_t v, int32_t* block_total) {
+  __shared__ int32_t warp_part[SCAN_THREADS / 32];
+  __shared__ int32_t total_s;
+  const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
+  int32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int32_t y = __shfl_up_sync(FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_part[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int32_t s = lane < SCAN_THREADS / 32 ? warp_part[lane] : 0;
+    int32_t t = s;
+#pragma unroll
+    for (int o = 1; o < SCAN_THREADS / 32; o <<= 1) {
+      int32_t y = __shfl_up_sync(FULL, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < SCAN_THREADS / 32) warp_part[lane] = t - s;
+    if (lane == SCAN_THREADS / 32 - 1) total_s = t;
+  }
+  __syncthreads();
+  int32_t r = x - v + warp_part[w];
+  *block_total = total_s;
+  __syncthreads();  // warp_part / total_s may be reused by the next call
+  return r;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS)
+scan_reduce_tiles(const int32_t* __restrict__ in, int64_t n, int32_t* __restrict__ sums) {
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+  int32_t s = 0;
+#pragma unroll
+  for (int j = 0; j < SCAN_ITEMS; ++j)
+    if (base + j < n) s += in[base + j];
+  int32_t tot;
+  block_exclusive_scan(s, &tot);
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// in == out allowed: each thread reads its items before writing them.
+__global__ void __launch_bounds__(SCAN_THREADS)
+scan_tiles(const int32_t* in, int32_t* out, int64_t n, const int32_t* __restrict__ tile_off,
+           int32_t* __restrict__ total) {
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+  int32_t v[SCAN_ITEMS];
+  int32_t s = 0;
+#pragma unroll
+  for (int j = 0; j < SCAN_ITEMS; ++j) {
+    v[j] = (base + j < n) ? in[base + j] : 0;
+    s += v[j];
+  }
+  int32_t tot;
+  int32_t run = block_exclusive_scan(s, &tot);
+  if (tile_off) run += tile_off[blockIdx.x];
+#pragma unroll
+  for (int j = 0; j < SCAN_ITEMS; ++j) {
+    if (base + j < n) out[base + j] = run;
+    run += v[j];
+  }
+  if (total && threadIdx.x == 0) *total = tot;
+}
+
+// ---------------------------------------------------------------------------
+// Radix sort (stable LSD, 8-bit digits, 4096-key tiles)
+// ---------------------------------------------------------------------------
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_ITEMS = 16;                     // keys per thread
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;   // 4096
+
+__global__ void __launch_bounds__(RS_THREADS)
+rs_hist(const uint64_t* __restrict__ keys, int64_t n, int shift, int32_t* __restrict__ hist,
+        int32_t ntiles) {
+  __shared__ int32_t cnt[256];
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+#pragma unroll 4
+  for (int j = 0; j < RS_ITEMS; ++j) {
+    int64_t k = base + j * RS_THREADS + threadIdx.x;
+    if (k < n) atomicAdd(&cnt[(unsigned)(keys[k] >> shift) & 255u], 1);
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// Each warp ranks a contiguous run of 512 keys in order, so the tile's order
+// (warp, round, lane) is the input order and the scatter is stable.
+__global__ void __launch_bounds__(RS_THREADS)
+rs_scatter(const uint64_t* __restrict__ keys, uint64_t* __restrict__ out, int64_t n, int shift,
+           const int32_t* __restrict__ hist_scanned, int32_t ntiles) {
+  __shared__ int32_t wcnt[RS_WARPS][256];
+  __shared__ int32_t toff[256];
+  for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) (&wcnt[0][0])[i] = 0;
+  toff[threadIdx.x] = hist_scanned[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  const int64_t base = (int64_t)blockIdx.x * RS_TILE + (int64_t)w * (32 * RS_ITEMS);
+  uint64_t kv[RS_ITEMS];
+  int32_t loc[RS_ITEMS];
+  int32_t dg[RS_ITEMS];
+#pragma unroll
+  for (int j = 0; j < RS_ITEMS; ++j) {
+    const int64_t k = base + j * 32 + lane;
+    const bool valid = k < n;
+    const uint64_t key = valid ? keys[k] : 0ull;
+    const int d = valid ? (int)((unsigned)(key >> shift) & 255u) : 256;
+    const unsigned peers = __match_any_sync(FULL, d);
+    const int rank = __popc(peers & lt);
+    const int32_t b = valid ? wcnt[w][d] : 0;
+    __syncwarp();
+    if (valid && rank == 0) wcnt[w][d] = b + __popc(peers);
+    __syncwarp();
+    kv[j] = key;
+    loc[j] = b + rank;
+    dg[j] = d;
+  }
+  __syncthreads();
+  {
+    int32_t run = 0;
+#pragma unroll
+    for (int q = 0; q < RS_WARPS; ++q) {
+      int32_t c = wcnt[q][threadIdx.x];
+      wcnt[q][threadIdx.x] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < RS_ITEMS; ++j) {
+    if (dg[j] < 256) out[toff[dg[j]] + wcnt[w][dg[j]] + loc[j]] = kv[j];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Misc
+// ---------------------------------------------------------------------------
+
+__global__ void fill_i32_kernel(int32_t* p, int32_t v, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+// key = (col << 32) | row for every CSR entry (warp per row).
+__global__ void pack_col_row(int32_t n_rows, const int32_t* __restrict__ row_ptr,
+                             const int32_t* __restrict__ cols, uint64_t* __restrict__ keys) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < n_rows;
+       r += warps) {
+    const int32_t b = row_ptr[r], e = row_ptr[r + 1];
+    for (int32_t k = b + lane; k < e; k += 32)
+      keys[k] = ((uint64_t)(uint32_t)cols[k] << 32) | (uint32_t)r;
+  }
+}
+
+__global__ void count_high(const uint64_t* __restrict__ keys, int64_t n, int32_t* __restrict__ cnt) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&cnt[(uint32_t)(keys[i] >> 32)], 1);
+}
+
+__global__ void low_words(const uint64_t* __restrict__ keys, int64_t n, int32_t* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (int32_t)(uint32_t)keys[i];
+}
+
+}  // namespace
+
+int exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, int32_t* total,
+                       cudaStream_t s) {
+  if (n <= 0) {
+    if (total) HNV_CUDA(cudaMemsetAsync(total, 0, sizeof(int32_t), s));
+    return HNV_OK;
+  }
+  const int64_t nt = (n + SCAN_TILE - 1) / SCAN_TILE;
+  if (nt == 1)
+    return launch("scan_tiles", scan_tiles, 1, SCAN_THREADS, 0, s, in, out, n,
+                  (const int32_t*)nullptr, total);
+  TempPool pool(s);
+  int32_t* sums = nullptr;
+  HNV_CHECK(pool.get(&sums, (size_t)nt));
+  HNV_CHECK(launch("scan_reduce_tiles", scan_reduce_tiles, (unsigned)nt, SCAN_THREADS, 0, s,
+                   in, n, sums));
+  HNV_CHECK(exclusive_scan_i32(sums, sums, nt, total, s));
+  return launch("scan_tiles", scan_tiles, (unsigned)nt, SCAN_THREADS, 0, s, in, out, n,
+                (const int32_t*)sums, (int32_t*)nullptr);
+}
+
+int bits_for_count(int64_t count) {
+  int b = 0;
+  while (b < 63 && (int64_t(1) << b) < count) ++b;
+  return b;
+}
+
+int radix_shifts(int low_bits, int high_bits, int* shifts) {
+  int k = 0;
+  for (int b = 0; b < low_bits; b += 8) shifts[k++] = b;
+  for (int b = 0; b < high_bits; b += 8) shifts[k++] = 32 + b;
+  return k;
+}
+
+int radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, const int* shifts, int npasses,
+                   cudaStream_t s, uint64_t** result) {
+  *result = keys;
+  if (n <= 1 || npasses == 0) return HNV_OK;
+  const int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
+  if (ntiles * 256 >= (int64_t(1) << 31)) HNV_FAIL(HNV_ERR_TOO_LARGE, "radix sort too large");
+  TempPool pool(s);
+  int32_t* hist = nullptr;
+  HNV_CHECK(pool.get(&hist, (size_t)(ntiles * 256)));
+  uint64_t* src = keys;
+  uint64_t* dst = alt;
+  for (int p = 0; p < npasses; ++p) {
+    HNV_CHECK(launch("rs_hist", rs_hist, (unsigned)ntiles, RS_THREADS, 0, s,
+                     (const uint64_t*)src, n, shifts[p], hist, (int32_t)ntiles));
+    HNV_CHECK(exclusive_scan_i32(hist, hist, ntiles * 256, nullptr, s));
+    HNV_CHECK(launch("rs_scatter", rs_scatter, (unsigned)ntiles, RS_THREADS, 0, s,
+                     (const uint64_t*)src, dst, n, shifts[p], (const int32_t*)hist,
+                     (int32_t)ntiles));
+    uint64_t* t = src;
+    src = dst;
+    dst = t;
+  }
+  *result = src;
+  return HNV_OK;
+}
+
+int fill_i32(int32_t* p, int32_t value, int64_t n, cudaStream_t s) {
+  if (n <= 0) return HNV_OK;
+  return launch("fill_i32", fill_i32_kernel, grid_for(n, 256), 256, 0, s, p, value, n);
+}
+
+int transpose_csr(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t* row_ptr,
+                  const int32_t* cols, int32_t* col_ptr, int32_t* col_rows, cudaStream_t s) {
+  TempPool pool(s);
+  int32_t* cnt = nullptr;
+  HNV_CHECK(pool.get(&cnt, (size_t)n_cols + 1));
+  HNV_CUDA(cudaMemsetAsync(cnt, 0, ((size_t)n_cols + 1) * sizeof(int32_t), s));
+  if (nnz > 0) {
+    uint64_t *k0 = nullptr, *k1 = nullptr, *sorted = nullptr;
+    HNV_CHECK(pool.get(&k0, (size_t)nnz));
+    HNV_CHECK(pool.get(&k1, (size_t)nnz));
+    HNV_CHECK(launch("pack_col_row", pack_col_row, grid_for((int64_t)n_rows * 32, 256), 256, 0, s,
+                     n_rows, row_ptr, cols, k0));
+    int shifts[16];
+    int np = radix_shifts(0, bits_for_count(n_cols), shifts);
+    HNV_CHECK(radix_sort_u64(k0, k1, nnz, shifts, np, s, &sorted));
+    HNV_CHECK(launch("count_high", count_high, grid_for(nnz, 256), 256, 0, s,
+                     (const uint64_t*)sorted, nnz, cnt));
+    HNV_CHECK(launch("low_words", low_words, grid_for(nnz, 256), 256, 0, s,
+                     (const uint64_t*)sorted, nnz, col_rows));
+  }
+  return exclusive_scan_i32(cnt, col_ptr, (int64_t)n_cols + 1, nullptr, s);
+}
+
+}  // namespace hnv
