@@ -1,0 +1,465 @@
+"""Benchmark of the HyperNetVec V-cycle hot path on GB300.
+
+One step = the whole hot path over the 1M-node planted-community workload
+(1,000,000 nodes, 1,000,000 hyperedges, sizes 2+Zipf(1.8) capped at 5,000,
+weights U[0.5,2), d=128, 20 two-phase sweeps per level, coarsened to
+<= 10,000 nodes): build the incidence (level 0), coarsen level by level,
+refine the coarsest level from the seeded embedding, then project and refine
+every finer level.
+
+Metric: refinement updates per second, where one update is one incidence
+times one embedding element (sum over levels of 2 * nnz_l * d * sweeps per
+step), divided by the whole step time (build and coarsening included).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Prints one JSON line (rank 0).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import hypergen  # noqa: E402
+
+METRIC = "refine incidence-nnz×d updates/s"
+UNIT = "updates/s"
+WORKLOAD = "planted_1m"
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (replicas: one independent V-cycle per GPU)
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def init_dist(ws, backend):
+    import torch.distributed as dist
+    if ws > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend)
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int, device=None) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(units_per_rank: float, seconds: list) -> float:
+    """Whole-job throughput: units of all ranks over the slowest rank."""
+    return units_per_rank * len(seconds) / max(seconds)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.uuid = uuid
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        cmd = ["nvidia-smi", "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if self.uuid:
+            cmd += ["--id=" + self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, mx, power = [], [], []
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 10:
+                continue
+            try:
+                sm.append(float(f[2]))
+                mx.append(float(f[3]))
+                power.append(float(f[4]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[6:10]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "power_w_max": float(max(power)), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (the cpu_baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+
+_SAMPLES = {}
+
+
+def oracle_sample(hg, spec, fraction: float = 1.0):
+    """One two-phase refinement sweep of level 0 by the FP64 oracle on the
+    first `fraction` of the hyperedges (all their members). Returns
+    (updates, seconds, description); the sample level is built once."""
+    from oracle import hnv_oracle as O
+    m_s = max(1, int(round(hg.m * fraction)))
+    key = (id(hg), m_s, spec.d)
+    if key not in _SAMPLES:
+        nnz_s = int(hg.edge_ptr[m_s])
+        lv = O.build_level(hg.n, m_s, hg.edge_ptr[:m_s + 1], hg.edge_nodes[:nnz_s],
+                           hg.weights[:m_s])
+        rng = np.random.default_rng(7)
+        _SAMPLES[key] = (lv, rng.standard_normal((lv.n, spec.d)),
+                         rng.standard_normal((lv.m, spec.d)))
+    lv, z_v, z_e = _SAMPLES[key]
+    t0 = time.perf_counter()
+    O.refine(lv, z_v, z_e, 0.5, 1, O.SWEEP_TWO_PHASE)
+    dt = time.perf_counter() - t0
+    upd = 2.0 * lv.nnz * spec.d
+    desc = ("one two-phase refinement sweep of level 0 restricted to the first %d of %d "
+            "hyperedges (nnz %d, d %d), FP64 numpy/scipy oracle" % (m_s, hg.m, lv.nnz, spec.d))
+    return upd, dt, desc
+
+
+def oracle_threads() -> int:
+    # scipy's CSR product and numpy elementwise ops run on one thread here
+    return 1
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+
+def source_hash(path):
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def load_traffic(kernel_tag):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        rec = json.load(open(p)).get(kernel_tag)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_2103_09660_gb300", "csrc", "refine.cu")
+    if rec.get("source_sha256_16") != source_hash(src):
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p)), "measured"
+        except ValueError:
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    import paper_2103_09660_gb300 as H
+    from paper_2103_09660_gb300 import build as B
+
+    if ws > 1:
+        init_dist(ws, "nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B.build()
+    H.lib()
+    spec = hypergen.CONFIGS[args.workload]
+    hg = hypergen.generate(spec)
+    stream = torch.cuda.current_stream()
+
+    d_ptr = torch.from_numpy(hg.edge_ptr).to(dev)
+    d_nodes = torch.from_numpy(hg.edge_nodes).to(dev)
+    d_w = torch.from_numpy(hg.weights).to(dev)
+
+    # learn the hierarchy once (deterministic), then seed the coarsest level
+    with H.Graph(hg.n, hg.m, d_ptr, d_nodes, d_w) as G:
+        L = G.coarsen(min_nodes=spec.min_nodes, max_levels=spec.max_levels, seed=spec.seed)
+        sizes = [G.level_info(l) for l in range(L)]
+    n_L, m_L, _ = sizes[-1]
+    zc_host = hypergen.coarsest_embedding(n_L + m_L, spec.d, seed=spec.seed)
+    d_zc = torch.from_numpy(zc_host).to(dev)
+    z_v = torch.empty((hg.n, spec.d), device=dev)
+    z_e = torch.empty((hg.m, spec.d), device=dev)
+    updates = float(sum(2.0 * nnz * spec.d * spec.sweeps for (_, _, nnz) in sizes))
+
+    def step():
+        g = H.hnv_build_incidence(hg.n, hg.m, d_ptr, d_nodes, d_w, stream)
+        try:
+            H.hnv_coarsen(g, seed=spec.seed, min_nodes=spec.min_nodes, max_levels=spec.max_levels)
+            H.hnv_vcycle(g, d_zc, z_v, z_e, 0.5, spec.sweeps, H.SWEEP_TWO_PHASE, stream)
+        finally:
+            H.lib().hnv_graph_free(g)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: inputs resident in HBM ----
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+    H.timing_reset()
+    H.timing_enable(True)
+    launches0 = H.kernel_launch_count()
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clock_rec = clocks.stop()
+    launches = H.kernel_launch_count() - launches0
+    H.timing_enable(False)
+    sec = ev0.elapsed_time(ev1) / 1e3
+    sec_max = max_over_ranks(sec, ws, dev)
+    phases = {}
+    for name, ph in (("build", H.PHASE_BUILD), ("coarsen", H.PHASE_COARSEN),
+                     ("project", H.PHASE_PROJECT), ("refine_e", H.PHASE_REFINE_E),
+                     ("refine_v", H.PHASE_REFINE_V)):
+        ms, cnt, by = H.timing_read(ph)
+        phases[name] = {"ms_per_step": ms / args.steps, "launches": cnt, "alg_bytes": by}
+
+    # ---- end to end through the public API: host buffers, copies inside ----
+    pin_ptr = torch.from_numpy(hg.edge_ptr).pin_memory().numpy()
+    pin_nodes = torch.from_numpy(hg.edge_nodes).pin_memory().numpy()
+    pin_w = torch.from_numpy(hg.weights).pin_memory().numpy()
+    pin_zc = torch.from_numpy(zc_host).pin_memory().numpy()
+    out_v = torch.empty((hg.n, spec.d), dtype=torch.float32).pin_memory().numpy()
+    out_e = torch.empty((hg.m, spec.d), dtype=torch.float32).pin_memory().numpy()
+
+    def step_host():
+        g = H.hnv_build_incidence(hg.n, hg.m, pin_ptr, pin_nodes, pin_w, stream)
+        try:
+            H.hnv_coarsen(g, seed=spec.seed, min_nodes=spec.min_nodes, max_levels=spec.max_levels)
+            H.hnv_vcycle(g, pin_zc, out_v, out_e, 0.5, spec.sweeps, H.SWEEP_TWO_PHASE, stream)
+        finally:
+            H.lib().hnv_graph_free(g)
+
+    e2e_steps = max(1, min(args.steps, 5))
+    step_host()
+    torch.cuda.synchronize()
+    barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        step_host()
+    torch.cuda.synchronize()
+    e2e_sec = (time.perf_counter() - t0) / e2e_steps
+    e2e_max = max_over_ranks(e2e_sec, ws, dev)
+    h2d = hg.edge_ptr.nbytes + hg.edge_nodes.nbytes + hg.weights.nbytes + zc_host.nbytes
+    d2h = out_v.nbytes + out_e.nbytes
+
+    if rank != 0:
+        return None
+
+    # ---- roofline of the dominant kernel (the heavier refinement half-sweep) ----
+    peaks, peak_src = measured_peaks()
+    dom = max(("refine_e", "refine_v"), key=lambda k: phases[k]["ms_per_step"])
+    ms_tot = phases[dom]["ms_per_step"] * args.steps
+    achieved = phases[dom]["alg_bytes"] / (ms_tot / 1e3) / 1e9 if ms_tot > 0 else 0.0
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    tag = "refine_v_half_sweep" if dom == "refine_v" else "refine_e_half_sweep"
+    traffic = load_traffic(tag)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "kernel": tag + " (gather_kernel + finalize_kernel)",
+                "peak_source": peak_src + " hbm_gbs (copy bandwidth)",
+                "bytes": "compulsory: neighbour table once, own rows read+written, indices, "
+                         "pointers, weights, normalisers"}
+
+    # ---- CPU oracle on a bounded sample ----
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        upd, dt, desc = oracle_sample(hg, spec, 1.0)
+        cpu = {"value": upd / dt, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
+               "sample": desc, "seconds": round(dt, 2),
+               "host_cores_available": len(os.sched_getaffinity(0))}
+
+    value = aggregate(updates, [sec_max / args.steps] * ws)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sec_max / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n": hg.n, "m": hg.m, "nnz": hg.nnz, "d": spec.d,
+                   "sweeps_per_level": spec.sweeps, "omega": 0.5, "sweep": "two_phase",
+                   "levels": len(sizes), "level_sizes": [list(s) for s in sizes],
+                   "updates_per_step": updates,
+                   "l2": "inputs larger than L2 (node and hyperedge embeddings 512 MB each)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "vcycle_ms": sec_max / args.steps * 1e3,
+        "phase_ms_per_step": {k: round(v["ms_per_step"], 3) for k, v in phases.items()},
+        "refine_only_updates_per_s": updates / ((phases["refine_e"]["ms_per_step"] +
+                                                 phases["refine_v"]["ms_per_step"]) / 1e3),
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": aggregate(updates, [e2e_max] * ws), "unit": UNIT,
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "ms_per_step": e2e_max * 1e3, "steps": e2e_steps},
+        "gpu_launches": int(launches),
+        "clocks": clock_rec,
+    }
+    return line
+
+
+def run_reference(args, ws, rank, local):
+    """The reference arm: the CPU FP64 oracle on host cores, rank 0 only."""
+    if rank != 0:
+        return None
+    spec = hypergen.CONFIGS[args.workload]
+    hg = hypergen.generate(spec)
+    # size the per-step sample so warm-up + timed steps stay within ~3 minutes
+    upd1, dt1, _ = oracle_sample(hg, spec, 0.02)
+    per_full = dt1 / 0.02
+    frac = min(1.0, 150.0 / (max(1, args.steps + args.warmup) * per_full))
+    for _ in range(args.warmup):
+        oracle_sample(hg, spec, frac)
+    tot_u, tot_t = 0.0, 0.0
+    desc = ""
+    for _ in range(args.steps):
+        u, t, desc = oracle_sample(hg, spec, frac)
+        tot_u += u
+        tot_t += t
+    value = tot_u / tot_t
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_t / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n": hg.n, "m": hg.m, "nnz": hg.nnz, "d": spec.d},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def run_refine_level(args):
+    """Profiling aid: build and coarsen the workload up to `level`, then run
+    `sweeps` two-phase sweeps of that level on random rows, and print the
+    per-half-sweep device times. Few launches precede the refinement, which
+    keeps ncu captures of it short."""
+    import torch
+    import paper_2103_09660_gb300 as H
+    from paper_2103_09660_gb300 import build as B
+    B.build()
+    spec = hypergen.CONFIGS[args.workload]
+    hg = hypergen.generate(spec)
+    with H.Graph.from_hypergraph(hg, on_device=True) as G:
+        if args.refine_level > 0:
+            G.coarsen(min_nodes=spec.min_nodes, max_levels=args.refine_level, seed=spec.seed)
+        lvl = min(args.refine_level, G.num_levels - 1)
+        n, m, nnz = G.level_info(lvl)
+        gen = torch.Generator(device="cuda").manual_seed(0)
+        z_v = torch.randn((n, spec.d), device="cuda", generator=gen)
+        z_e = torch.randn((m, spec.d), device="cuda", generator=gen)
+        torch.cuda.synchronize()
+        H.timing_reset()
+        H.timing_enable(True)
+        G.refine(lvl, z_v, z_e, 0.5, args.sweeps)
+        torch.cuda.synchronize()
+        H.timing_enable(False)
+        out = {"level": lvl, "n": n, "m": m, "nnz": nnz, "d": spec.d, "sweeps": args.sweeps}
+        for nm, ph in (("refine_e", H.PHASE_REFINE_E), ("refine_v", H.PHASE_REFINE_V)):
+            ms, c, by = H.timing_read(ph)
+            out[nm] = {"ms_per_launch": ms / max(c, 1),
+                       "alg_GBps": by / (ms / 1e3) / 1e9 if ms > 0 else 0.0}
+        print(json.dumps(out))
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(hypergen.CONFIGS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--refine-level", type=int, default=None,
+                    help="profiling aid: only refine this level (see run_refine_level)")
+    ap.add_argument("--sweeps", type=int, default=2)
+    args = ap.parse_args(argv)
+    ws, rank, local = dist_env()
+    if args.refine_level is not None:
+        run_refine_level(args)
+        return
+    if args.impl == "reference":
+        line = run_reference(args, ws, rank, local)
+    else:
+        line = run_ours(args, ws, rank, local)
+    if line is not None and rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        if dist.is_initialized():
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
