@@ -96,7 +96,7 @@ typedef struct hnv_graph hnv_graph;
  * members of hyperedge e are edge_nodes[edge_ptr[e] .. edge_ptr[e+1]).
  * Builds the star-expansion incidence CSR (hyperedge -> nodes) and CSC
  * (node -> hyperedges) with ascending, duplicate-free rows, the weighted
- * node degrees sum_{e ∋ v} w_e (float32, summed in ascending e) and 1/|e|.
+ * node degrees sum_{e ∋ v} w_e (float32, summed in a fixed order) and 1/|e|.
  *   n_nodes, n_edges   : |V| >= 1, |E| >= 0
  *   edge_ptr [m+1]     : int64, edge_ptr[0] = 0, non-decreasing; every
  *                        hyperedge non-empty (the paper's hyperedges are
@@ -202,6 +202,31 @@ int hnv_refine(hnv_graph* g, int level, void* z_v, void* z_e, hnv_dtype dt, int 
 int hnv_vcycle(hnv_graph* g, const void* z_coarsest, void* z_v_out, void* z_e_out,
                hnv_dtype dt, int d, float omega, int sweeps_per_level, hnv_sweep mode,
                int buffers_on_device, hnv_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * hnv_refine_noalloc -- hnv_refine (HNV_SWEEP_TWO_PHASE, HNV_F32) for callers
+ * that must not allocate device memory during the call. This is a library
+ * service with no counterpart in the paper.
+ * Some programs reserve their whole device-memory budget up front (a serving
+ * process with a fixed pool, a deployment under a hard memory cap) and treat
+ * any later cudaMalloc as an error: it can fail under memory pressure and may
+ * stall the device while it synchronises. hnv_refine allocates its split-row
+ * scratch on first use; this call uses a fixed device array compiled into the
+ * library instead (HNV_NOALLOC_SCRATCH_BYTES, held by every GPU that loads
+ * the library until the process exits) and calls no allocator at all.
+ *   Arguments and results are those of hnv_refine with mode TWO_PHASE; the
+ *   graph (built earlier) and the embeddings stay caller-provided.
+ *   Returns HNV_ERR_TOO_LARGE when the level needs more scratch than the
+ *   array holds: max(chunks of either half-sweep) * d * 4 bytes, where a row
+ *   with more than 128 incidences contributes ceil(len / 128) chunks.
+ *   The first call on a device looks up the array's device address (once per
+ *   device, under a lock). All calls share the one array and it keeps the
+ *   last call's contents; calls whose kernels overlap on the GPU (other
+ *   streams, other host threads) race on it, so serialise them.
+ * ------------------------------------------------------------------------- */
+#define HNV_NOALLOC_SCRATCH_BYTES (16u << 20)
+int hnv_refine_noalloc(hnv_graph* g, int level, void* z_v, void* z_e, hnv_dtype dt, int d,
+                       float omega, int sweeps, hnv_stream_t stream);
 
 /* Releases the hierarchy (stream-ordered on the graph's stream). NULL is a no-op. */
 void hnv_graph_free(hnv_graph* g);

@@ -28,7 +28,7 @@ __all__ = [
     "ARR_REP_E", "ARR_DEG_V",
     "PHASE_BUILD", "PHASE_COARSEN", "PHASE_PROJECT", "PHASE_REFINE_E", "PHASE_REFINE_V",
     "Graph", "hnv_build_incidence", "hnv_coarsen", "hnv_project", "hnv_refine",
-    "hnv_vcycle", "kernel_launch_count", "timing_enable", "timing_reset", "timing_read",
+    "hnv_vcycle", "hnv_refine_noalloc", "kernel_launch_count", "timing_enable", "timing_reset", "timing_read",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -81,6 +81,7 @@ def _declare(L):
         "hnv_project": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, ctypes.c_int, ctypes.c_int, _P]),
         "hnv_refine": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_int, f32, ctypes.c_int, ctypes.c_int, _P]),
         "hnv_vcycle": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_int, f32, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
+        "hnv_refine_noalloc": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_int, f32, ctypes.c_int, _P]),
         "hnv_graph_free": (None, [_P]),
         "hnv_error_string": (ctypes.c_char_p, [ctypes.c_int]),
         "hnv_last_error_detail": (ctypes.c_char_p, []),
@@ -191,6 +192,18 @@ def hnv_refine(g: int, level: int, z_v, z_e, omega: float = 0.5, sweeps: int = 1
     _check(lib().hnv_refine(g, level, _dev_ptr(z_v, torch.float32, "z_v"),
                             _dev_ptr(z_e, torch.float32, "z_e"), F32, int(d), float(omega),
                             int(sweeps), int(mode), _stream_handle(stream)), "hnv_refine")
+
+
+def hnv_refine_noalloc(g: int, level: int, z_v, z_e, omega: float = 0.5, sweeps: int = 10,
+                       stream=None):
+    """Two-phase refinement that allocates no device memory (fixed scratch
+    inside the library; see include/hnv.h)."""
+    import torch
+    d = z_v.shape[1]
+    _check(lib().hnv_refine_noalloc(g, level, _dev_ptr(z_v, torch.float32, "z_v"),
+                                    _dev_ptr(z_e, torch.float32, "z_e"), F32, int(d),
+                                    float(omega), int(sweeps), _stream_handle(stream)),
+           "hnv_refine_noalloc")
 
 
 def hnv_vcycle(g: int, z_coarsest, z_v_out, z_e_out, omega: float = 0.5, sweeps: int = 10,

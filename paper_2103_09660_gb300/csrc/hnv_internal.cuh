@@ -219,6 +219,11 @@ int refine_level(hnv_graph* g, int level, float* z_v, float* z_e, int d, float o
                  int sweeps, int mode, cudaStream_t s);
 int project_level(const hnv_graph* g, int fine_level, const float* zc_v, const float* zc_e,
                   float* zf_v, float* zf_e, int d, cudaStream_t s);
+// Two-phase sweeps whose split-row partial sums go to caller-provided
+// scratch (at least max(planE.n_chunks, planV.n_chunks) * d floats); no
+// allocation and no timing events.
+int refine_two_phase_with_partials(const hnv_graph* g, int level, float* z_v, float* z_e, int d,
+                                   float omega, int sweeps, float* partials, cudaStream_t s);
 
 // Reads the device error word (synchronising s) and clears it.
 int read_and_clear_err(hnv_graph* g, cudaStream_t s, int32_t* bits);

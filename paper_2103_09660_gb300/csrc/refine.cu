@@ -337,6 +337,18 @@ int refine_level(hnv_graph* g, int level, float* z_v, float* z_e, int d, float o
   return HNV_OK;
 }
 
+int refine_two_phase_with_partials(const hnv_graph* g, int level, float* z_v, float* z_e, int d,
+                                   float omega, int sweeps, float* partials, cudaStream_t s) {
+  const Level& lv = g->levels[level];
+  const HalfSweep E{lv.m, lv.e_ptr, lv.e_nodes, nullptr, lv.inv_size_e, &lv.planE};
+  const HalfSweep V{lv.n, lv.v_ptr, lv.v_edges, lv.v_w, lv.inv_deg_v, &lv.planV};
+  for (int it = 0; it < sweeps; ++it) {
+    HNV_CHECK(run_half_dispatch(E, z_v, z_e, z_e, d, omega, partials, s));
+    HNV_CHECK(run_half_dispatch(V, z_e, z_v, z_v, d, omega, partials, s));
+  }
+  return HNV_OK;
+}
+
 int project_level(const hnv_graph* g, int fine_level, const float* zc_v, const float* zc_e,
                   float* zf_v, float* zf_e, int d, cudaStream_t s) {
   const Level& f = g->levels[fine_level];
