@@ -228,6 +228,12 @@ int hnv_vcycle(hnv_graph* g, const void* z_coarsest, void* z_v_out, void* z_e_ou
 int hnv_refine_noalloc(hnv_graph* g, int level, void* z_v, void* z_e, hnv_dtype dt, int d,
                        float omega, int sweeps, hnv_stream_t stream);
 
+/* Synchronises `stream` and reports device-side failures of the graph's
+ * asynchronous calls since the last check: HNV_ERR_TIMEOUT if a bounded
+ * device wait of a refinement kernel gave up (its results are then invalid),
+ * HNV_ERR_CUDA for a CUDA error, else HNV_OK. Clears the recorded failure. */
+int hnv_sync_status(hnv_graph* g, hnv_stream_t stream);
+
 /* Releases the hierarchy (stream-ordered on the graph's stream). NULL is a no-op. */
 void hnv_graph_free(hnv_graph* g);
 

@@ -83,6 +83,7 @@ def _declare(L):
         "hnv_vcycle": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_int, f32, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
         "hnv_refine_noalloc": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_int, f32, ctypes.c_int, _P]),
         "hnv_graph_free": (None, [_P]),
+        "hnv_sync_status": (ctypes.c_int, [_P, _P]),
         "hnv_error_string": (ctypes.c_char_p, [ctypes.c_int]),
         "hnv_last_error_detail": (ctypes.c_char_p, []),
         "hnv_set_allocator": (ctypes.c_int, [_P, _P, _P]),
@@ -286,6 +287,11 @@ class Graph:
 
     def __exit__(self, *exc):
         self.close()
+
+    def sync_status(self):
+        """Synchronise the graph's stream and raise if a device-side wait of
+        an asynchronous call gave up (HNV_ERR_TIMEOUT)."""
+        _check(lib().hnv_sync_status(self.handle, _stream_handle(self.stream)), "hnv_sync_status")
 
     def coarsen(self, **kw) -> int:
         return hnv_coarsen(self.handle, **kw)

@@ -111,6 +111,10 @@ int vcycle_impl(hnv_graph* g, const float* z_coarsest, float* z_v_out, float* z_
     if (l0.m > 0)
       HNV_CUDA(cudaMemcpyAsync(z_e_out, out_e, row_bytes * l0.m, cudaMemcpyDeviceToHost, s));
     HNV_CUDA(cudaStreamSynchronize(s));
+    int32_t bits = 0;
+    HNV_CHECK(read_and_clear_err(g, s, &bits));
+    if (bits & ERRBIT_TIMEOUT)
+      HNV_FAIL(HNV_ERR_TIMEOUT, "a bounded wait of a refinement kernel gave up");
   }
   return HNV_OK;
 }
@@ -387,6 +391,18 @@ int hnv_vcycle(hnv_graph* g, const void* z_coarsest, void* z_v_out, void* z_e_ou
   return vcycle_impl(g, (const float*)z_coarsest, (float*)z_v_out, (float*)z_e_out, d, omega,
                      sweeps_per_level, (int)mode, buffers_on_device,
                      reinterpret_cast<cudaStream_t>(stream));
+}
+
+int hnv_sync_status(hnv_graph* g, hnv_stream_t stream) {
+  if (!g) HNV_FAIL(HNV_ERR_INVALID_ARG, "graph is NULL");
+  DeviceGuard dgd(g->device);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  HNV_CUDA(cudaStreamSynchronize(s));
+  int32_t bits = 0;
+  HNV_CHECK(read_and_clear_err(g, s, &bits));
+  if (bits & ERRBIT_TIMEOUT)
+    HNV_FAIL(HNV_ERR_TIMEOUT, "a bounded wait of a refinement kernel gave up");
+  return HNV_OK;
 }
 
 void hnv_graph_free(hnv_graph* g) {

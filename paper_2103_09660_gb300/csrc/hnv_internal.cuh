@@ -45,7 +45,8 @@ enum : int32_t {
   ERRBIT_NODE_RANGE = 1,    // an input node ID outside [0, n)
   ERRBIT_EMPTY_EDGE = 2,    // an input hyperedge with no members
   ERRBIT_BAD_WEIGHT = 4,    // a weight that is not finite and > 0
-  ERRBIT_BAD_PTR = 8        // edge_ptr not starting at 0 / decreasing
+  ERRBIT_BAD_PTR = 8,       // edge_ptr not starting at 0 / decreasing
+  ERRBIT_TIMEOUT = 16       // a bounded device wait gave up (refinement)
 };
 
 // ---------------------------------------------------------------------------
@@ -155,16 +156,27 @@ int transpose_csr(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t* ro
 // The hierarchy
 // ---------------------------------------------------------------------------
 
-// Work plan of one half-sweep: rows longer than `T` incidences are split into
-// chunks of at most T consecutive incidences whose partial sums are reduced
-// in chunk order by a second kernel.
+// Work plan of one half-sweep (one side of the star expansion).
+// Rows are put in classes by length: A (1..4 incidences), B (5..16),
+// C (17..64), D (65..T); longer rows are cut into chunks of T consecutive
+// incidences whose partial sums a second kernel reduces in chunk order.
+// `items` holds one descriptor per work item {row, first incidence, length,
+// partial slot or -1}: the A rows, then B, C, D, then every chunk. Split
+// rows are listed in `long_desc` {row, first chunk, chunk count, 0}: those
+// with at most kMidChunks chunks first, then the rest. Rows of length 0 are
+// in zero_rows.
+constexpr int32_t kSplitT = 128;
+constexpr int32_t kMidChunks = 32;
+
 struct SplitPlan {
-  int32_t T = 0;
-  int32_t n_long = 0;
-  int32_t n_chunks = 0;
-  int32_t* long_rows = nullptr;   // [n_long]
-  int32_t* chunk_ptr = nullptr;   // [n_long + 1]
-  int2* chunk_range = nullptr;    // [n_chunks] (begin, end) incidence ranges
+  int32_t T = kSplitT;
+  int32_t n_a = 0, n_b = 0, n_c = 0, n_d = 0;  // rows per class
+  int32_t n_chunks = 0;                        // chunk items (after the D rows)
+  int32_t n_mid = 0, n_huge = 0;               // split rows by chunk count
+  int32_t n_zero = 0;
+  int4* items = nullptr;              // [n_a + n_b + n_c + n_d + n_chunks]
+  int4* long_desc = nullptr;          // [n_mid + n_huge]
+  int32_t* zero_rows = nullptr;       // [n_zero]
 };
 
 struct Level {
@@ -219,6 +231,13 @@ int refine_level(hnv_graph* g, int level, float* z_v, float* z_e, int d, float o
                  int sweeps, int mode, cudaStream_t s);
 int project_level(const hnv_graph* g, int fine_level, const float* zc_v, const float* zc_e,
                   float* zf_v, float* zf_e, int d, cudaStream_t s);
+// tma_refine.cu: TMA-gather half-sweep for d in {32, 64, 128, 256}.
+bool tma_supported(int d);
+int tma_half_sweep(const SplitPlan& plan, const int32_t* idx, const float* inc_w,
+                   const float* inv_norm, const float* src, int64_t src_rows, const float* self_in,
+                   float* out, int64_t self_rows, int d, float omega, float* partials,
+                   int32_t* err, cudaStream_t s);
+
 // Two-phase sweeps whose split-row partial sums go to caller-provided
 // scratch (at least max(planE.n_chunks, planV.n_chunks) * d floats); no
 // allocation and no timing events.

@@ -9,9 +9,6 @@
 
 namespace hnv {
 
-// Rows with more incidences than this are split into chunks (see SplitPlan).
-constexpr int32_t kSplitT = 128;
-
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
@@ -119,34 +116,76 @@ __global__ void deg_kernel(int32_t n, const int32_t* __restrict__ v_ptr,
   }
 }
 
-__global__ void long_flags_kernel(int32_t rows, const int32_t* __restrict__ ptr, int32_t T,
-                                  int32_t* __restrict__ is_long, int32_t* __restrict__ nchunk) {
+// Row class for the refinement plan: 0 empty, 1 A (1..4), 2 B (5..16),
+// 3 C (17..64), 4 D (65..T), 5 split into at most mid_chunks chunks, 6 split
+// into more.
+constexpr int kClasses = 7;
+
+__global__ void classify_rows(int32_t rows, const int32_t* __restrict__ ptr, int32_t T,
+                              int32_t mid_chunks, uint64_t* __restrict__ keys,
+                              int32_t* __restrict__ counts) {
+  __shared__ int32_t h[kClasses];
+  if (threadIdx.x < kClasses) h[threadIdx.x] = 0;
+  __syncthreads();
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows;
        r += (int64_t)gridDim.x * blockDim.x) {
     const int32_t d = ptr[r + 1] - ptr[r];
-    const bool l = d > T;
-    is_long[r] = l ? 1 : 0;
-    nchunk[r] = l ? (d + T - 1) / T : 0;
+    int c;
+    if (d == 0) c = 0;
+    else if (d <= 4) c = 1;
+    else if (d <= 16) c = 2;
+    else if (d <= 64) c = 3;
+    else if (d <= T) c = 4;
+    else c = ((d + T - 1) / T <= mid_chunks) ? 5 : 6;
+    keys[r] = ((uint64_t)c << 32) | (uint32_t)r;
+    atomicAdd(&h[c], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x < kClasses && h[threadIdx.x]) atomicAdd(&counts[threadIdx.x], h[threadIdx.x]);
+}
+
+__global__ void fill_row_items(const uint64_t* __restrict__ keys, int32_t begin, int32_t count,
+                               const int32_t* __restrict__ ptr, int4* __restrict__ items) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = (int32_t)(uint32_t)keys[begin + i];
+    const int32_t b = ptr[r];
+    items[i] = make_int4(r, b, ptr[r + 1] - b, -1);
   }
 }
 
-__global__ void fill_plan_kernel(int32_t rows, const int32_t* __restrict__ ptr, int32_t T,
-                                 const int32_t* __restrict__ is_long,
-                                 const int32_t* __restrict__ long_idx,
-                                 const int32_t* __restrict__ chunk_off,
-                                 int32_t* __restrict__ long_rows, int32_t* __restrict__ chunk_ptr,
-                                 int2* __restrict__ ranges) {
-  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows;
-       r += (int64_t)gridDim.x * blockDim.x) {
-    if (!is_long[r]) continue;
-    const int32_t i = long_idx[r];
-    long_rows[i] = (int32_t)r;
-    const int32_t c0 = chunk_off[r];
-    chunk_ptr[i] = c0;
-    const int32_t b = ptr[r], e = ptr[r + 1];
-    int32_t c = c0;
-    for (int32_t s = b; s < e; s += T, ++c) ranges[c] = make_int2(s, min(s + T, e));
+__global__ void long_chunk_counts(const uint64_t* __restrict__ keys, int32_t begin, int32_t count,
+                                  const int32_t* __restrict__ ptr, int32_t T,
+                                  int32_t* __restrict__ nch) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = (int32_t)(uint32_t)keys[begin + i];
+    nch[i] = (ptr[r + 1] - ptr[r] + T - 1) / T;
   }
+}
+
+__global__ void fill_long(const uint64_t* __restrict__ keys, int32_t begin, int32_t count,
+                          const int32_t* __restrict__ ptr, int32_t T,
+                          const int32_t* __restrict__ chunk_off, int4* __restrict__ long_desc,
+                          int4* __restrict__ chunk_items) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = (int32_t)(uint32_t)keys[begin + i];
+    const int32_t b = ptr[r], e = ptr[r + 1];
+    const int32_t c0 = chunk_off[i];
+    const int32_t nc = (e - b + T - 1) / T;
+    long_desc[i] = make_int4(r, c0, nc, 0);
+    for (int32_t j = 0; j < nc; ++j) {
+      const int32_t s = b + j * T;
+      chunk_items[c0 + j] = make_int4(r, s, min(T, e - s), c0 + j);
+    }
+  }
+}
+
+__global__ void key_rows(const uint64_t* __restrict__ keys, int32_t count, int32_t* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (int32_t)(uint32_t)keys[i];
 }
 
 }  // namespace
@@ -178,35 +217,57 @@ int read_and_clear_err(hnv_graph* g, cudaStream_t s, int32_t* bits) {
 
 static int build_plan(hnv_graph* g, Level* lv, const int32_t* ptr, int32_t rows, SplitPlan* plan,
                       cudaStream_t s) {
-  plan->T = kSplitT;
+  *plan = SplitPlan();
+  const int32_t T = plan->T;
+  if (rows == 0) return HNV_OK;
   TempPool pool(s);
-  int32_t *is_long = nullptr, *nchunk = nullptr;
-  HNV_CHECK(pool.get(&is_long, (size_t)rows + 1));
-  HNV_CHECK(pool.get(&nchunk, (size_t)rows + 1));
-  HNV_CHECK(launch("long_flags", long_flags_kernel, grid_for(rows, 256), 256, 0, s, rows, ptr,
-                   kSplitT, is_long, nchunk));
-  int32_t* tot = g->d_buf;
-  HNV_CHECK(exclusive_scan_i32(is_long, is_long, rows, tot, s));   // is_long -> long index
-  HNV_CHECK(exclusive_scan_i32(nchunk, nchunk, rows, tot + 1, s)); // nchunk -> chunk offset
-  int32_t h[2];
-  HNV_CHECK(read_ints(g, tot, 2, h, s));
-  plan->n_long = h[0];
-  plan->n_chunks = h[1];
-  if (plan->n_long == 0) return HNV_OK;
-  // the scans overwrote the flags; recompute them into a fresh buffer
-  int32_t *flag = nullptr, *dummy = nullptr;
-  HNV_CHECK(pool.get(&flag, (size_t)rows + 1));
-  HNV_CHECK(pool.get(&dummy, (size_t)rows + 1));
-  HNV_CHECK(launch("long_flags", long_flags_kernel, grid_for(rows, 256), 256, 0, s, rows, ptr,
-                   kSplitT, flag, dummy));
-  HNV_CHECK(level_alloc(lv, (void**)&plan->long_rows, sizeof(int32_t) * plan->n_long, s));
-  HNV_CHECK(level_alloc(lv, (void**)&plan->chunk_ptr, sizeof(int32_t) * (plan->n_long + 1), s));
-  HNV_CHECK(level_alloc(lv, (void**)&plan->chunk_range, sizeof(int2) * plan->n_chunks, s));
-  HNV_CHECK(launch("fill_plan", fill_plan_kernel, grid_for(rows, 256), 256, 0, s, rows, ptr,
-                   kSplitT, (const int32_t*)flag, (const int32_t*)is_long,
-                   (const int32_t*)nchunk, plan->long_rows, plan->chunk_ptr, plan->chunk_range));
-  HNV_CUDA(cudaMemcpyAsync(plan->chunk_ptr + plan->n_long, &tot[1], sizeof(int32_t),
-                           cudaMemcpyDeviceToDevice, s));
+  uint64_t *k0 = nullptr, *k1 = nullptr, *sorted = nullptr;
+  HNV_CHECK(pool.get(&k0, (size_t)rows));
+  HNV_CHECK(pool.get(&k1, (size_t)rows));
+  int32_t* cnt = g->d_buf;
+  HNV_CUDA(cudaMemsetAsync(cnt, 0, 16 * sizeof(int32_t), s));
+  HNV_CHECK(launch("classify_rows", classify_rows, grid_for(rows, 256), 256, 0, s, rows, ptr, T,
+                   kMidChunks, k0, cnt));
+  const int shift = 32;
+  HNV_CHECK(radix_sort_u64(k0, k1, rows, &shift, 1, s, &sorted));   // stable: rows ascend per class
+  int32_t c[kClasses];
+  HNV_CHECK(read_ints(g, cnt, kClasses, c, s));
+  int32_t off[kClasses + 1] = {0};
+  for (int i = 0; i < kClasses; ++i) off[i + 1] = off[i] + c[i];
+  plan->n_zero = c[0];
+  plan->n_a = c[1];
+  plan->n_b = c[2];
+  plan->n_c = c[3];
+  plan->n_d = c[4];
+  plan->n_mid = c[5];
+  plan->n_huge = c[6];
+  const int32_t n_rows_items = c[1] + c[2] + c[3] + c[4];
+  const int32_t n_long = c[5] + c[6];
+  int32_t* chunk_off = nullptr;
+  if (n_long > 0) {
+    HNV_CHECK(pool.get(&chunk_off, (size_t)n_long));
+    HNV_CHECK(launch("long_chunk_counts", long_chunk_counts, grid_for(n_long, 256), 256, 0, s,
+                     (const uint64_t*)sorted, off[5], n_long, ptr, T, chunk_off));
+    HNV_CHECK(exclusive_scan_i32(chunk_off, chunk_off, n_long, cnt + 8, s));
+    HNV_CHECK(read_ints(g, cnt + 8, 1, &plan->n_chunks, s));
+  }
+  const int64_t n_items = (int64_t)n_rows_items + plan->n_chunks;
+  if (n_items > 0)
+    HNV_CHECK(level_alloc(lv, (void**)&plan->items, sizeof(int4) * (size_t)n_items, s));
+  if (n_rows_items > 0)
+    HNV_CHECK(launch("fill_row_items", fill_row_items, grid_for(n_rows_items, 256), 256, 0, s,
+                     (const uint64_t*)sorted, off[1], n_rows_items, ptr, plan->items));
+  if (n_long > 0) {
+    HNV_CHECK(level_alloc(lv, (void**)&plan->long_desc, sizeof(int4) * (size_t)n_long, s));
+    HNV_CHECK(launch("fill_long", fill_long, grid_for(n_long, 256), 256, 0, s,
+                     (const uint64_t*)sorted, off[5], n_long, ptr, T, (const int32_t*)chunk_off,
+                     plan->long_desc, plan->items + n_rows_items));
+  }
+  if (plan->n_zero > 0) {
+    HNV_CHECK(level_alloc(lv, (void**)&plan->zero_rows, sizeof(int32_t) * (size_t)plan->n_zero, s));
+    HNV_CHECK(launch("key_rows", key_rows, grid_for(plan->n_zero, 256), 256, 0, s,
+                     (const uint64_t*)sorted, plan->n_zero, plan->zero_rows));
+  }
   return HNV_OK;
 }
 

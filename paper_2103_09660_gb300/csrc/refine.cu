@@ -7,14 +7,21 @@
 // It is a sparse-rows-times-dense-rows gather, HBM-bound (about 0.5 flop per
 // gathered byte): no tensor-core work exists here.
 //
-// Work decomposition (gather_kernel): a group of G lanes owns one row; each
-// lane holds VPL float4 columns (G * VPL * 4 >= d). The group loads G
-// neighbour indices with one coalesced access, broadcasts them by shuffle,
-// and issues U independent 16-byte row loads per lane before accumulating
-// them in incidence order (fixed order: results are deterministic). Rows
-// longer than T incidences are cut into chunks of T; each chunk is one work
-// item writing an un-normalised partial sum, and finalize_kernel reduces a
-// row's partials in chunk order and applies the relaxation.
+// Work decomposition. Each half-sweep has a plan of work items (SplitPlan):
+// rows of 1..4, 5..16 and 17..T incidences (classes A, B, C) and chunks of
+// at most T incidences cut from longer rows. gather_kernel<G, VPL, W> gives
+// each item a group of G lanes (R = 32/G items per warp at once); each lane
+// holds VPL float4 columns (G * VPL * 4 >= d). Class A runs with G = 8,
+// B with 16, C and chunks with 32 (for d = 128), so a warp works on up to
+// four short rows at once. A group loads its item descriptor (16 bytes) and
+// its own row early, loads G neighbour indices with one coalesced access,
+// broadcasts them by shuffle and issues U independent 16-byte row loads per
+// lane before accumulating them in incidence order (fixed order: results are
+// deterministic, no atomics). A chunk writes its un-normalised partial sum;
+// finalize_kernel reduces a split row's partials in chunk order and applies
+// the relaxation.
+#include <cstdlib>
+
 #include "hnv_internal.cuh"
 
 namespace hnv {
@@ -47,47 +54,38 @@ __device__ __forceinline__ float4 relax4(float keep, float sc, const float4& sel
 
 template <int G, int VPL, bool WEIGHTED>
 __global__ void __launch_bounds__(256)
-gather_kernel(int32_t n_rows, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+gather_kernel(const int4* __restrict__ items, int32_t n_items, const int32_t* __restrict__ idx,
               const float* __restrict__ inc_w, const float* __restrict__ inv_norm,
               const float4* __restrict__ src, const float4* self_in, float4* out, int32_t d4,
-              float omega, int32_t T, int32_t n_chunks, const int2* __restrict__ chunk_range,
-              float4* __restrict__ partials) {
-  constexpr int R = 32 / G;                                   // rows per warp pass
-  constexpr int UB = (VPL == 1) ? 8 : (VPL == 2 ? 4 : 2);     // row loads in flight
+              float omega, float4* __restrict__ partials) {
+  constexpr int R = 32 / G;                                    // items per warp pass
+  // row loads in flight per lane (the weighted variant also holds a weight
+  // per load, so it takes half as many to keep its register count down)
+  constexpr int UB0 = (VPL == 1) ? 8 : (VPL == 2 ? 4 : (VPL == 4 ? 2 : 1));
+  constexpr int UB = (WEIGHTED && UB0 > 1) ? UB0 / 2 : UB0;
   constexpr int U = UB < G ? UB : G;
   const int lane = threadIdx.x & 31;
   const int grp = lane / G;
   const int lg = lane & (G - 1);
   const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
-  const int64_t n_items = (int64_t)n_rows + n_chunks;
   const float keep = 1.0f - omega;
 
   for (int64_t wbase = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * R;
        wbase < n_items; wbase += warps_total * R) {
     const int64_t item = wbase + grp;
-    int32_t beg = 0, len = 0, row = -1, chunk = -1;
-    bool copy_only = false;
-    if (item < n_rows) {
-      const int32_t r = (int32_t)item;
-      const int32_t b = ptr[r], e = ptr[r + 1];
-      const int32_t dg = e - b;
-      if (dg == 0) {
-        if (self_in != out) {   // out-of-place (Jacobi): carry the row over
-          copy_only = true;
-          row = r;
-        }
-      } else if (dg <= T) {
-        row = r;
-        beg = b;
-        len = dg;
-      }
-    } else if (item < n_items) {
-      chunk = (int32_t)(item - n_rows);
-      const int2 cr = chunk_range[chunk];
-      beg = cr.x;
-      len = cr.y - cr.x;
-    }
+    int4 it = make_int4(-1, 0, 0, -1);
+    if (item < n_items) it = __ldg(items + item);
+    const int32_t row = it.x, beg = it.y, len = it.z, slot = it.w;
+    const bool is_row = (row >= 0) && (slot < 0);
 
+    float4 sv[VPL];
+    if (is_row) {
+#pragma unroll
+      for (int j = 0; j < VPL; ++j) {
+        const int col = lg + j * G;
+        sv[j] = (col < d4) ? self_in[(size_t)row * d4 + col] : f4_zero();
+      }
+    }
     float4 acc[VPL];
 #pragma unroll
     for (int j = 0; j < VPL; ++j) acc[j] = f4_zero();
@@ -130,76 +128,104 @@ gather_kernel(int32_t n_rows, const int32_t* __restrict__ ptr, const int32_t* __
       }
     }
 
-    if (row >= 0) {
-      const float sc = copy_only ? 0.f : omega * inv_norm[row];
+    if (is_row) {
+      const float sc = omega * inv_norm[row];
 #pragma unroll
       for (int j = 0; j < VPL; ++j) {
         const int col = lg + j * G;
-        if (col < d4) {
-          const size_t o = (size_t)row * d4 + col;
-          const float4 sv = self_in[o];
-          out[o] = copy_only ? sv : relax4(keep, sc, sv, acc[j]);
-        }
+        if (col < d4) out[(size_t)row * d4 + col] = relax4(keep, sc, sv[j], acc[j]);
       }
-    } else if (chunk >= 0) {
+    } else if (slot >= 0) {
 #pragma unroll
       for (int j = 0; j < VPL; ++j) {
         const int col = lg + j * G;
-        if (col < d4) partials[(size_t)chunk * d4 + col] = acc[j];
+        if (col < d4) partials[(size_t)slot * d4 + col] = acc[j];
       }
     }
   }
 }
 
-// One block per long row: S = blockDim / d4 slices each sum a contiguous
-// run of the row's chunk partials (four interleaved accumulators), then
-// slice 0 adds the slices in order and applies the relaxation.
+// Reduces the chunk partials of split rows in chunk order and relaxes.
+// Blocks [0, mid_blocks) give one warp to each of the first n_mid rows (at
+// most kMidChunks chunks: lanes over columns, four interleaved
+// accumulators); each later block takes one of the n_huge rows: S =
+// blockDim / d4 slices sum contiguous runs of chunks (four interleaved
+// accumulators each) and slice 0 adds the slices in order.
 constexpr int kFinThreads = 1024;
 
+__device__ __forceinline__ float4 sum_strided4(const float4* __restrict__ p, int32_t count,
+                                               int32_t stride) {
+  float4 a0 = f4_zero(), a1 = f4_zero(), a2 = f4_zero(), a3 = f4_zero();
+  int32_t c = 0;
+  for (; c + 4 <= count; c += 4) {
+    const float4 p0 = p[(size_t)c * stride];
+    const float4 p1 = p[(size_t)(c + 1) * stride];
+    const float4 p2 = p[(size_t)(c + 2) * stride];
+    const float4 p3 = p[(size_t)(c + 3) * stride];
+    f4_add(a0, p0);
+    f4_add(a1, p1);
+    f4_add(a2, p2);
+    f4_add(a3, p3);
+  }
+  for (; c < count; ++c) f4_add(a0, p[(size_t)c * stride]);
+  f4_add(a0, a1);
+  f4_add(a2, a3);
+  f4_add(a0, a2);
+  return a0;
+}
+
 __global__ void __launch_bounds__(kFinThreads)
-finalize_kernel(int32_t n_long, const int32_t* __restrict__ long_rows,
-                const int32_t* __restrict__ chunk_ptr, const float4* __restrict__ partials,
+finalize_kernel(const int4* __restrict__ long_desc, int32_t n_mid, int32_t n_huge,
+                int32_t mid_blocks, const float4* __restrict__ partials,
                 const float* __restrict__ inv_norm, const float4* self_in, float4* out,
                 int32_t d4, float omega) {
   extern __shared__ float4 sm[];
+  const float keep = 1.0f - omega;
+  if ((int32_t)blockIdx.x < mid_blocks) {
+    const int32_t k = blockIdx.x * (kFinThreads / 32) + (threadIdx.x >> 5);
+    if (k >= n_mid) return;
+    const int4 ds = long_desc[k];
+    const int lane = threadIdx.x & 31;
+    const float sc = omega * inv_norm[ds.x];
+    for (int col = lane; col < d4; col += 32) {
+      const float4 tot = sum_strided4(partials + (size_t)ds.y * d4 + col, ds.z, d4);
+      const size_t o = (size_t)ds.x * d4 + col;
+      out[o] = relax4(keep, sc, self_in[o], tot);
+    }
+    return;
+  }
+  const int32_t k = n_mid + (int32_t)blockIdx.x - mid_blocks;
+  if (k >= n_mid + n_huge) return;
+  const int4 ds = long_desc[k];
   const int S = (int)blockDim.x / d4;
   const int t = threadIdx.x;
   const int slice = t / d4;
   const int col = t - slice * d4;
-  const float keep = 1.0f - omega;
-  for (int64_t k = blockIdx.x; k < n_long; k += gridDim.x) {
-    const int32_t row = long_rows[k];
-    const int32_t c0 = chunk_ptr[k], c1 = chunk_ptr[k + 1];
-    const int64_t nc = c1 - c0;
-    if (slice < S) {
-      const int32_t a = c0 + (int32_t)(nc * slice / S);
-      const int32_t b = c0 + (int32_t)(nc * (slice + 1) / S);
-      float4 a0 = f4_zero(), a1 = f4_zero(), a2 = f4_zero(), a3 = f4_zero();
-      int32_t c = a;
-      for (; c + 4 <= b; c += 4) {
-        const float4 p0 = partials[(size_t)c * d4 + col];
-        const float4 p1 = partials[(size_t)(c + 1) * d4 + col];
-        const float4 p2 = partials[(size_t)(c + 2) * d4 + col];
-        const float4 p3 = partials[(size_t)(c + 3) * d4 + col];
-        f4_add(a0, p0);
-        f4_add(a1, p1);
-        f4_add(a2, p2);
-        f4_add(a3, p3);
-      }
-      for (; c < b; ++c) f4_add(a0, partials[(size_t)c * d4 + col]);
-      f4_add(a0, a1);
-      f4_add(a2, a3);
-      f4_add(a0, a2);
-      sm[slice * d4 + col] = a0;
-    }
-    __syncthreads();
-    if (slice == 0) {
-      float4 tot = sm[col];
-      for (int q = 1; q < S; ++q) f4_add(tot, sm[q * d4 + col]);
-      const size_t o = (size_t)row * d4 + col;
-      out[o] = relax4(keep, omega * inv_norm[row], self_in[o], tot);
-    }
-    __syncthreads();
+  if (slice < S) {
+    const int32_t a = (int32_t)((int64_t)ds.z * slice / S);
+    const int32_t b = (int32_t)((int64_t)ds.z * (slice + 1) / S);
+    sm[slice * d4 + col] = sum_strided4(partials + (size_t)(ds.y + a) * d4 + col, b - a, d4);
+  }
+  __syncthreads();
+  if (slice == 0) {
+    float4 tot = sm[col];
+    for (int q = 1; q < S; ++q) f4_add(tot, sm[q * d4 + col]);
+    const size_t o = (size_t)ds.x * d4 + col;
+    out[o] = relax4(keep, omega * inv_norm[ds.x], self_in[o], tot);
+  }
+}
+
+// Out-of-place sweeps (Jacobi): rows without neighbours carry over.
+__global__ void copy_rows_kernel(const int32_t* __restrict__ rows, int32_t n_rows,
+                                 const float4* __restrict__ src, float4* __restrict__ dst,
+                                 int32_t d4) {
+  const int64_t total = (int64_t)n_rows * d4;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = i / d4;
+    const int32_t col = (int32_t)(i - k * d4);
+    const size_t o = (size_t)rows[k] * d4 + col;
+    dst[o] = src[o];
   }
 }
 
@@ -228,58 +254,112 @@ __global__ void project_kernel(int32_t n, int32_t m, const int32_t* __restrict__
 // ---------------------------------------------------------------------------
 
 struct HalfSweep {
-  int32_t rows;
-  const int32_t* ptr;
   const int32_t* idx;
   const float* inc_w;      // null: unweighted (hyperedge side)
   const float* inv_norm;
   const SplitPlan* plan;
+  int64_t src_rows;        // rows of the neighbour table
+  int64_t self_rows;       // rows of this side's table
+  int32_t* err;            // device error word (bounded waits)
 };
 
+// Which gather path the half-sweeps use. The default is the per-lane load
+// path (gather_kernel). HNV_GATHER=tma selects the TMA-gather path
+// (tma_refine.cu) where it has a variant for d; both compute the same sums.
+// Measured on the 1M-node workload the TMA path is slower (per-row tensor
+// copies of 512-byte rows cap its throughput), so it is opt-in.
+bool use_tma(int d) {
+  static int mode = -1;
+  if (mode < 0) {
+    const char* e = getenv("HNV_GATHER");
+    mode = (e && e[0] == 't') ? 1 : 0;
+  }
+  return mode == 1 && tma_supported(d);
+}
+
 template <int G, int VPL>
-int run_half(const HalfSweep& h, const float* src, const float* self_in, float* out, int d4,
-             float omega, float* partials, cudaStream_t s) {
+int launch_items(const HalfSweep& h, const int4* items, int32_t n_items, const float* src,
+                 const float* self_in, float* out, int d4, float omega, float* partials,
+                 cudaStream_t s) {
+  if (n_items <= 0) return HNV_OK;
   constexpr int R = 32 / G;
-  const int64_t items = (int64_t)h.rows + h.plan->n_chunks;
-  const int64_t warps = (items + R - 1) / R;
+  const int64_t warps = ((int64_t)n_items + R - 1) / R;
   const int64_t blocks64 = (warps + 7) / 8;
   const unsigned blocks = (unsigned)(blocks64 > 0x7fffffff ? 0x7fffffff : blocks64);
-  if (h.inc_w) {
-    HNV_CHECK(launch("gather_w", gather_kernel<G, VPL, true>, blocks, 256, 0, s, h.rows, h.ptr,
-                     h.idx, h.inc_w, h.inv_norm, (const float4*)src, (const float4*)self_in,
-                     (float4*)out, d4, omega, h.plan->T, h.plan->n_chunks,
-                     (const int2*)h.plan->chunk_range, (float4*)partials));
-  } else {
-    HNV_CHECK(launch("gather", gather_kernel<G, VPL, false>, blocks, 256, 0, s, h.rows, h.ptr,
-                     h.idx, h.inc_w, h.inv_norm, (const float4*)src, (const float4*)self_in,
-                     (float4*)out, d4, omega, h.plan->T, h.plan->n_chunks,
-                     (const int2*)h.plan->chunk_range, (float4*)partials));
-  }
-  if (h.plan->n_long > 0) {
-    const int S = kFinThreads / d4;
-    const size_t smem = sizeof(float4) * (size_t)S * d4;
-    const unsigned fb = (unsigned)(h.plan->n_long < 65535 * 16 ? h.plan->n_long : 65535 * 16);
-    HNV_CHECK(launch("finalize", finalize_kernel, fb, kFinThreads, smem, s, h.plan->n_long,
-                     (const int32_t*)h.plan->long_rows, (const int32_t*)h.plan->chunk_ptr,
-                     (const float4*)partials, h.inv_norm, (const float4*)self_in, (float4*)out,
-                     d4, omega));
-  }
-  return HNV_OK;
+  if (h.inc_w)
+    return launch("gather_w", gather_kernel<G, VPL, true>, blocks, 256, 0, s, items, n_items,
+                  h.idx, h.inc_w, h.inv_norm, (const float4*)src, (const float4*)self_in,
+                  (float4*)out, d4, omega, (float4*)partials);
+  return launch("gather", gather_kernel<G, VPL, false>, blocks, 256, 0, s, items, n_items, h.idx,
+                h.inc_w, h.inv_norm, (const float4*)src, (const float4*)self_in, (float4*)out,
+                d4, omega, (float4*)partials);
+}
+
+int launch_items_dispatch(int G, int VPL, const HalfSweep& h, const int4* items, int32_t n_items,
+                          const float* src, const float* self_in, float* out, int d4,
+                          float omega, float* partials, cudaStream_t s) {
+#define HNV_CASE(g, v)                                                                 \
+  if (G == g && VPL == v)                                                              \
+    return launch_items<g, v>(h, items, n_items, src, self_in, out, d4, omega, partials, s);
+  HNV_CASE(1, 1) HNV_CASE(2, 1) HNV_CASE(4, 1)
+  HNV_CASE(8, 1) HNV_CASE(8, 2) HNV_CASE(8, 4) HNV_CASE(8, 8)
+  HNV_CASE(16, 1) HNV_CASE(16, 2) HNV_CASE(16, 4) HNV_CASE(16, 8)
+  HNV_CASE(32, 1) HNV_CASE(32, 2) HNV_CASE(32, 4) HNV_CASE(32, 8)
+#undef HNV_CASE
+  HNV_FAIL(HNV_ERR_UNSUPPORTED_D, "no gather variant for G=%d VPL=%d", G, VPL);
+}
+
+int next_pow2(int x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+// Lanes per item for a class whose natural width is `cls` lanes: at most the
+// row width in float4s (rounded up to a power of two), at least enough that
+// a lane holds no more than 8 float4s.
+int group_lanes(int cls, int d4) {
+  int g = cls < next_pow2(d4) ? cls : next_pow2(d4);
+  const int gmin = next_pow2((d4 + 7) / 8);
+  if (g < gmin) g = gmin;
+  return g > 32 ? 32 : g;
 }
 
 int run_half_dispatch(const HalfSweep& h, const float* src, const float* self_in, float* out,
                       int d, float omega, float* partials, cudaStream_t s) {
   const int d4 = d / 4;
-  if (d4 <= 1) return run_half<1, 1>(h, src, self_in, out, d4, omega, partials, s);
-  if (d4 <= 2) return run_half<2, 1>(h, src, self_in, out, d4, omega, partials, s);
-  if (d4 <= 4) return run_half<4, 1>(h, src, self_in, out, d4, omega, partials, s);
-  if (d4 <= 8) return run_half<8, 1>(h, src, self_in, out, d4, omega, partials, s);
-  if (d4 <= 16) return run_half<16, 1>(h, src, self_in, out, d4, omega, partials, s);
-  if (d4 <= 32) return run_half<32, 1>(h, src, self_in, out, d4, omega, partials, s);
-  if (d4 <= 64) return run_half<32, 2>(h, src, self_in, out, d4, omega, partials, s);
-  if (d4 <= 128) return run_half<32, 4>(h, src, self_in, out, d4, omega, partials, s);
-  if (d4 <= 256) return run_half<32, 8>(h, src, self_in, out, d4, omega, partials, s);
-  HNV_FAIL(HNV_ERR_UNSUPPORTED_D, "d = %d is larger than 1024", d);
+  if (d4 < 1 || d4 > 256) HNV_FAIL(HNV_ERR_UNSUPPORTED_D, "d = %d not in [4, 1024]", d);
+  const SplitPlan& p = *h.plan;
+  if (use_tma(d)) {
+    HNV_CHECK(tma_half_sweep(p, h.idx, h.inc_w, h.inv_norm, src, h.src_rows, self_in, out,
+                             h.self_rows, d, omega, partials, h.err, s));
+  } else {
+    const int4* items = p.items;
+    const int cls_lanes[3] = {8, 16, 32};
+    const int32_t counts[3] = {p.n_a, p.n_b, p.n_c + p.n_d + p.n_chunks};
+    int32_t off = 0;
+    for (int c = 0; c < 3; ++c) {
+      const int G = group_lanes(cls_lanes[c], d4);
+      const int VPL = next_pow2((d4 + G - 1) / G);
+      HNV_CHECK(launch_items_dispatch(G, VPL, h, items + off, counts[c], src, self_in, out, d4,
+                                      omega, partials, s));
+      off += counts[c];
+    }
+  }
+  if (p.n_mid + p.n_huge > 0) {
+    const int32_t mid_blocks = (p.n_mid + kFinThreads / 32 - 1) / (kFinThreads / 32);
+    const int S = kFinThreads / d4;
+    const size_t smem = sizeof(float4) * (size_t)S * d4;
+    HNV_CHECK(launch("finalize", finalize_kernel, (unsigned)(mid_blocks + p.n_huge), kFinThreads,
+                     smem, s, (const int4*)p.long_desc, p.n_mid, p.n_huge, mid_blocks,
+                     (const float4*)partials, h.inv_norm, (const float4*)self_in, (float4*)out,
+                     d4, omega));
+  }
+  if (self_in != out && p.n_zero > 0)
+    HNV_CHECK(launch("copy_rows", copy_rows_kernel, grid_for((int64_t)p.n_zero * d4, 256), 256, 0,
+                     s, (const int32_t*)p.zero_rows, p.n_zero, (const float4*)self_in,
+                     (float4*)out, d4));
+  return HNV_OK;
 }
 
 int ensure_scratch(float** p, size_t* have, size_t need, cudaStream_t s) {
@@ -305,8 +385,8 @@ int refine_level(hnv_graph* g, int level, float* z_v, float* z_e, int d, float o
   if (mode == HNV_SWEEP_JACOBI)
     HNV_CHECK(ensure_scratch(&g->jacobi_tmp, &g->jacobi_bytes,
                              sizeof(float) * ((size_t)lv.m > 0 ? lv.m : 1) * d, s));
-  const HalfSweep E{lv.m, lv.e_ptr, lv.e_nodes, nullptr, lv.inv_size_e, &lv.planE};
-  const HalfSweep V{lv.n, lv.v_ptr, lv.v_edges, lv.v_w, lv.inv_deg_v, &lv.planV};
+  const HalfSweep E{lv.e_nodes, nullptr, lv.inv_size_e, &lv.planE, lv.n, lv.m, g->d_err};
+  const HalfSweep V{lv.v_edges, lv.v_w, lv.inv_deg_v, &lv.planV, lv.m, lv.n, g->d_err};
   const double n = lv.n, m = lv.m, nnz = (double)lv.nnz;
   const double bytesE = 4.0 * (n * d + 2.0 * m * d + nnz + 2.0 * m + 1.0);
   const double bytesV = 4.0 * (m * d + 2.0 * n * d + 2.0 * nnz + 2.0 * n + 1.0);
@@ -340,8 +420,8 @@ int refine_level(hnv_graph* g, int level, float* z_v, float* z_e, int d, float o
 int refine_two_phase_with_partials(const hnv_graph* g, int level, float* z_v, float* z_e, int d,
                                    float omega, int sweeps, float* partials, cudaStream_t s) {
   const Level& lv = g->levels[level];
-  const HalfSweep E{lv.m, lv.e_ptr, lv.e_nodes, nullptr, lv.inv_size_e, &lv.planE};
-  const HalfSweep V{lv.n, lv.v_ptr, lv.v_edges, lv.v_w, lv.inv_deg_v, &lv.planV};
+  const HalfSweep E{lv.e_nodes, nullptr, lv.inv_size_e, &lv.planE, lv.n, lv.m, g->d_err};
+  const HalfSweep V{lv.v_edges, lv.v_w, lv.inv_deg_v, &lv.planV, lv.m, lv.n, g->d_err};
   for (int it = 0; it < sweeps; ++it) {
     HNV_CHECK(run_half_dispatch(E, z_v, z_e, z_e, d, omega, partials, s));
     HNV_CHECK(run_half_dispatch(V, z_e, z_v, z_v, d, omega, partials, s));

@@ -38,6 +38,11 @@ def _np(t):
     return t.double().cpu().numpy()
 
 
+def _ok(G):
+    """No device-side wait of the graph's kernels gave up."""
+    G.sync_status()
+
+
 # ---------------------------------------------------------------------------
 # Incidence build and coarsening: bit-exact
 # ---------------------------------------------------------------------------
@@ -127,6 +132,7 @@ def test_long_rows_and_skew(H):
                 for mode in (H.SWEEP_TWO_PHASE, H.SWEEP_JACOBI):
                     a, b = zv.clone(), ze.clone()
                     G.refine(ell, a, b, 0.5, 3, mode)
+                    _ok(G)
                     rv, re = O.refine(lvl, z[:lvl.n], z[lvl.n:], 0.5, 3, mode)
                     assert rel_err(_np(a), rv) < FP32_TOL
                     assert rel_err(_np(b), re) < FP32_TOL
@@ -146,6 +152,7 @@ def test_refine_one_level_widths(H, d):
         for mode in (H.SWEEP_TWO_PHASE, H.SWEEP_JACOBI):
             zv, ze = _t(z[:lv.n]), _t(z[lv.n:])
             G.refine(0, zv, ze, 0.5, 4, mode)
+            _ok(G)
             rv, re = O.refine(lv, z[:lv.n], z[lv.n:], 0.5, 4, mode)
             assert rel_err(_np(zv), rv) < FP32_TOL
             assert rel_err(_np(ze), re) < FP32_TOL
@@ -225,6 +232,7 @@ def test_vcycle_small_workload(H, mode):
         zv = torch.empty((hg.n, spec.d), device="cuda")
         ze = torch.empty((hg.m, spec.d), device="cuda")
         G.vcycle(_t(zc), zv, ze, 0.5, spec.sweeps, mode)
+        _ok(G)
         assert rel_err(_np(zv), ref.z_v) < FP32_TOL
         assert rel_err(_np(ze), ref.z_e) < FP32_TOL
         # host buffers: same result, copies inside the call
