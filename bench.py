@@ -237,10 +237,11 @@ def run_ours(args, ws, rank, local):
         L = G.coarsen(min_nodes=spec.min_nodes, max_levels=spec.max_levels, seed=spec.seed)
         sizes = [G.level_info(l) for l in range(L)]
     n_L, m_L, _ = sizes[-1]
-    zc_host = hypergen.coarsest_embedding(n_L + m_L, spec.d, seed=spec.seed)
-    d_zc = torch.from_numpy(zc_host).to(dev)
-    z_v = torch.empty((hg.n, spec.d), device=dev)
-    z_e = torch.empty((hg.m, spec.d), device=dev)
+    tdt = torch.bfloat16 if args.dtype == "bf16" else torch.float32
+    zc_t = torch.from_numpy(hypergen.coarsest_embedding(n_L + m_L, spec.d, seed=spec.seed)).to(tdt)
+    d_zc = zc_t.to(dev)
+    z_v = torch.empty((hg.n, spec.d), dtype=tdt, device=dev)
+    z_e = torch.empty((hg.m, spec.d), dtype=tdt, device=dev)
     updates = float(sum(2.0 * nnz * spec.d * spec.sweeps for (_, _, nnz) in sizes))
 
     def step():
@@ -291,9 +292,9 @@ def run_ours(args, ws, rank, local):
     pin_ptr = torch.from_numpy(hg.edge_ptr).pin_memory().numpy()
     pin_nodes = torch.from_numpy(hg.edge_nodes).pin_memory().numpy()
     pin_w = torch.from_numpy(hg.weights).pin_memory().numpy()
-    pin_zc = torch.from_numpy(zc_host).pin_memory().numpy()
-    out_v = torch.empty((hg.n, spec.d), dtype=torch.float32).pin_memory().numpy()
-    out_e = torch.empty((hg.m, spec.d), dtype=torch.float32).pin_memory().numpy()
+    pin_zc = zc_t.pin_memory()
+    out_v = torch.empty((hg.n, spec.d), dtype=tdt).pin_memory()
+    out_e = torch.empty((hg.m, spec.d), dtype=tdt).pin_memory()
 
     def step_host():
         g = H.hnv_build_incidence(hg.n, hg.m, pin_ptr, pin_nodes, pin_w, stream)
@@ -313,8 +314,9 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     e2e_sec = (time.perf_counter() - t0) / e2e_steps
     e2e_max = max_over_ranks(e2e_sec, ws, dev)
-    h2d = hg.edge_ptr.nbytes + hg.edge_nodes.nbytes + hg.weights.nbytes + zc_host.nbytes
-    d2h = out_v.nbytes + out_e.nbytes
+    h2d = (hg.edge_ptr.nbytes + hg.edge_nodes.nbytes + hg.weights.nbytes +
+           pin_zc.numel() * pin_zc.element_size())
+    d2h = (out_v.numel() + out_e.numel()) * out_v.element_size()
 
     if rank != 0:
         return None
@@ -346,13 +348,14 @@ def run_ours(args, ws, rank, local):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": sec_max / args.steps * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
         "data": "synthetic",
         "config": {"workload": args.workload, "n": hg.n, "m": hg.m, "nnz": hg.nnz, "d": spec.d,
                    "sweeps_per_level": spec.sweeps, "omega": 0.5, "sweep": "two_phase",
                    "levels": len(sizes), "level_sizes": [list(s) for s in sizes],
                    "updates_per_step": updates,
-                   "l2": "inputs larger than L2 (node and hyperedge embeddings 512 MB each)",
+                   "storage": "bf16 rows, f32 sums" if args.dtype == "bf16" else "f32",
+                   "l2": "inputs larger than L2 (node and hyperedge embedding tables)",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "vcycle_ms": sec_max / args.steps * 1e3,
         "phase_ms_per_step": {k: round(v["ms_per_step"], 3) for k, v in phases.items()},
@@ -433,6 +436,139 @@ def run_refine_level(args):
         print(json.dumps(out))
 
 
+# ---------------------------------------------------------------------------
+# Precision study: BF16 storage vs FP32 on the same GPU, and both vs the
+# FP64 oracle on an induced subsample
+# ---------------------------------------------------------------------------
+
+def _oracle_vcycle_cols(args):
+    """Oracle V-cycle on a block of embedding columns (refinement acts on each
+    column independently, so column blocks can run in separate processes)."""
+    hg_arrays, params, zc_block, sweeps = args
+    from oracle import hnv_oracle as O
+    n, m, ptr, nodes, w = hg_arrays
+    lv0 = O.build_level(n, m, ptr, nodes, w)
+    h = O.coarsen(lv0, O.CoarsenParams(**params))
+    res = O.vcycle(h, zc_block, 0.5, sweeps, keep_levels=True)
+    return [np.vstack(p) for p in res.per_level]
+
+
+def gpu_levels(H, G, zc, sweeps):
+    """The V-cycle run level by level through the ABI; returns each level's
+    refined rows (nodes then hyperedges) as device tensors."""
+    import torch
+    L = G.num_levels - 1
+    sizes = [G.level_info(l) for l in range(L + 1)]
+    out = [None] * (L + 1)
+    n, m, _ = sizes[L]
+    z = zc.clone()
+    G.refine(L, z[:n], z[n:], 0.5, sweeps)
+    out[L] = z
+    for l in range(L - 1, -1, -1):
+        n, m, _ = sizes[l]
+        zf = torch.empty((n + m, zc.shape[1]), dtype=zc.dtype, device=zc.device)
+        nc = sizes[l + 1][0]
+        G.project(l, out[l + 1][:nc], out[l + 1][nc:], zf[:n], zf[n:])
+        G.refine(l, zf[:n], zf[n:], 0.5, sweeps)
+        out[l] = zf
+    G.sync_status()
+    return out
+
+
+def level_errors(got, ref):
+    """(max |diff| / max |ref|, max row-relative error with the 1e-3 rms floor)."""
+    import torch
+    g = got.double()
+    r = ref.double() if hasattr(ref, "double") else torch.from_numpy(ref).to(g.device)
+    diff = (g - r).abs()
+    glob = float(diff.max() / r.abs().max())
+    rms = float(torch.sqrt((r * r).mean()))
+    den = torch.clamp(r.abs().max(dim=1).values, min=1e-3 * rms)
+    row = float((diff.max(dim=1).values / den).max())
+    return glob, row
+
+
+def run_precision_study(args):
+    import multiprocessing as mp
+    import torch
+    spec = hypergen.CONFIGS[args.workload]
+    hg = hypergen.generate(spec)
+    sub = hypergen.induced_subhypergraph(hg, min(args.subsample, hg.n), seed=spec.seed)
+    params = dict(min_nodes=spec.min_nodes, max_levels=spec.max_levels, seed=spec.seed)
+    # the seeded coarsest rows of the subsample, rounded to bfloat16 once:
+    # both GPU precisions and the oracle start from exactly these values
+    import paper_2103_09660_gb300 as H
+    from paper_2103_09660_gb300 import build as B
+    B.build()
+    dev = torch.device("cuda", 0)
+    with H.Graph.from_hypergraph(sub, on_device=True) as G:
+        L = G.coarsen(**params)
+        nL, mL, _ = G.level_info(L - 1)
+    zc = torch.from_numpy(hypergen.coarsest_embedding(nL + mL, spec.d, seed=spec.seed))
+    zc = zc.to(torch.bfloat16).float()
+    # oracle: column blocks in spawned workers
+    blocks = max(1, min(16, (os.cpu_count() or 1)))
+    cols = np.array_split(np.arange(spec.d), blocks)
+    arrays = (sub.n, sub.m, sub.edge_ptr, sub.edge_nodes, sub.weights)
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(blocks) as pool:
+        parts = pool.map(_oracle_vcycle_cols,
+                         [(arrays, params, zc.numpy()[:, c].astype(np.float64), spec.sweeps)
+                          for c in cols])
+    oracle_s = time.perf_counter() - t0
+    ref = [np.hstack([p[l] for p in parts]) for l in range(len(parts[0]))]
+    sub_rows = []
+    with H.Graph.from_hypergraph(sub, on_device=True) as G:
+        G.coarsen(**params)
+        z32 = gpu_levels(H, G, zc.to(dev), spec.sweeps)
+        z16 = gpu_levels(H, G, zc.to(dev).to(torch.bfloat16), spec.sweeps)
+        for l in range(len(ref)):
+            r = torch.from_numpy(ref[l]).to(dev)
+            sub_rows.append({"level": l, "fp32_vs_fp64": level_errors(z32[l], r),
+                             "bf16_vs_fp64": level_errors(z16[l], r)})
+    del z32, z16
+    # full size: timing and BF16 vs FP32 per level
+    full_rows = []
+    timing = {}
+    with H.Graph.from_hypergraph(hg, on_device=True) as G:
+        L = G.coarsen(**params)
+        sizes = [G.level_info(l) for l in range(L)]
+        nL, mL, _ = sizes[-1]
+        zc_full = torch.from_numpy(hypergen.coarsest_embedding(nL + mL, spec.d, seed=spec.seed))
+        zc_full = zc_full.to(torch.bfloat16).to(dev)
+        for name, dt in (("fp32", torch.float32), ("bf16", torch.bfloat16)):
+            zv = torch.empty((hg.n, spec.d), dtype=dt, device=dev)
+            ze = torch.empty((hg.m, spec.d), dtype=dt, device=dev)
+            zci = zc_full.to(dt)
+            G.vcycle(zci, zv, ze, 0.5, spec.sweeps)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.steps):
+                G.vcycle(zci, zv, ze, 0.5, spec.sweeps)
+            e1.record()
+            torch.cuda.synchronize()
+            G.sync_status()
+            timing[name] = e0.elapsed_time(e1) / args.steps
+            del zv, ze
+        z32 = gpu_levels(H, G, zc_full.float(), spec.sweeps)
+        z16 = gpu_levels(H, G, zc_full, spec.sweeps)
+        for l in range(L):
+            full_rows.append({"level": l, "n": sizes[l][0], "m": sizes[l][1], "nnz": sizes[l][2],
+                              "bf16_vs_fp32": level_errors(z16[l], z32[l])})
+    updates = float(sum(2.0 * nnz * spec.d * spec.sweeps for (_, _, nnz) in sizes))
+    print(json.dumps({
+        "study": "bf16 storage vs fp32", "workload": args.workload,
+        "n": hg.n, "m": hg.m, "nnz": hg.nnz, "d": spec.d, "sweeps_per_level": spec.sweeps,
+        "vcycle_ms": timing, "speedup_bf16_over_fp32": timing["fp32"] / timing["bf16"],
+        "refine_updates_per_s": {k: updates / (v / 1e3) for k, v in timing.items()},
+        "error_metrics": "(max|diff|/max|ref|, max row-relative with 1e-3 rms floor)",
+        "full_size_levels": full_rows,
+        "subsample": {"nodes": sub.n, "hyperedges": sub.m, "nnz": sub.nnz,
+                      "oracle_seconds": round(oracle_s, 1), "oracle_processes": blocks,
+                      "levels": sub_rows}}))
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -444,10 +580,19 @@ def main(argv=None):
     ap.add_argument("--refine-level", type=int, default=None,
                     help="profiling aid: only refine this level (see run_refine_level)")
     ap.add_argument("--sweeps", type=int, default=2)
+    ap.add_argument("--dtype", choices=["f32", "bf16"], default="f32",
+                    help="embedding storage of the timed V-cycle (sums are float32 either way)")
+    ap.add_argument("--precision-study", action="store_true",
+                    help="BF16 vs FP32 per level at full size, both vs the FP64 oracle on an "
+                         "induced subsample (use with --workload planted_4m)")
+    ap.add_argument("--subsample", type=int, default=250_000)
     args = ap.parse_args(argv)
     ws, rank, local = dist_env()
     if args.refine_level is not None:
         run_refine_level(args)
+        return
+    if args.precision_study:
+        run_precision_study(args)
         return
     if args.impl == "reference":
         line = run_reference(args, ws, rank, local)

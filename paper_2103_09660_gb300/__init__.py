@@ -134,6 +134,17 @@ def _dev_ptr(t, dtype, name: str, rows: Optional[int] = None, d: Optional[int] =
     return t.data_ptr()
 
 
+def _emb_dtype(t):
+    """(hnv dtype code, torch dtype) of an embedding tensor: float32 -> F32,
+    bfloat16 -> BF16 (stored as bfloat16, summed in float32)."""
+    import torch
+    if t.dtype == torch.float32:
+        return F32, torch.float32
+    if t.dtype == torch.bfloat16:
+        return BF16, torch.bfloat16
+    raise TypeError("embeddings must be float32 or bfloat16, got %s" % t.dtype)
+
+
 # ---------------------------------------------------------------------------
 # Entry points (same names as the C ABI)
 # ---------------------------------------------------------------------------
@@ -177,22 +188,21 @@ def hnv_coarsen(g: int, policy: int = ASSIGN_HASH, seed: int = 0, min_nodes: int
 
 
 def hnv_project(g: int, fine_level: int, zc_v, zc_e, zf_v, zf_e, stream=None):
-    import torch
-    d = zf_v.shape[1] if zf_v.dim() == 2 else zc_v.shape[1]
-    _check(lib().hnv_project(g, fine_level, _dev_ptr(zc_v, torch.float32, "zc_v"),
-                             _dev_ptr(zc_e, torch.float32, "zc_e"),
-                             _dev_ptr(zf_v, torch.float32, "zf_v"),
-                             _dev_ptr(zf_e, torch.float32, "zf_e"), F32, int(d),
+    dt, tdt = _emb_dtype(zf_v)
+    d = zf_v.shape[1]
+    _check(lib().hnv_project(g, fine_level, _dev_ptr(zc_v, tdt, "zc_v"),
+                             _dev_ptr(zc_e, tdt, "zc_e"), _dev_ptr(zf_v, tdt, "zf_v"),
+                             _dev_ptr(zf_e, tdt, "zf_e"), dt, int(d),
                              _stream_handle(stream)), "hnv_project")
 
 
 def hnv_refine(g: int, level: int, z_v, z_e, omega: float = 0.5, sweeps: int = 10,
                mode: int = SWEEP_TWO_PHASE, stream=None):
-    import torch
+    dt, tdt = _emb_dtype(z_v)
     d = z_v.shape[1]
-    _check(lib().hnv_refine(g, level, _dev_ptr(z_v, torch.float32, "z_v"),
-                            _dev_ptr(z_e, torch.float32, "z_e"), F32, int(d), float(omega),
-                            int(sweeps), int(mode), _stream_handle(stream)), "hnv_refine")
+    _check(lib().hnv_refine(g, level, _dev_ptr(z_v, tdt, "z_v"), _dev_ptr(z_e, tdt, "z_e"), dt,
+                            int(d), float(omega), int(sweeps), int(mode),
+                            _stream_handle(stream)), "hnv_refine")
 
 
 def hnv_refine_noalloc(g: int, level: int, z_v, z_e, omega: float = 0.5, sweeps: int = 10,
@@ -209,22 +219,32 @@ def hnv_refine_noalloc(g: int, level: int, z_v, z_e, omega: float = 0.5, sweeps:
 
 def hnv_vcycle(g: int, z_coarsest, z_v_out, z_e_out, omega: float = 0.5, sweeps: int = 10,
                mode: int = SWEEP_TWO_PHASE, stream=None):
-    """Device tensors (asynchronous) or numpy arrays (host; synchronous)."""
+    """Buffers are CUDA tensors (asynchronous), or host buffers: numpy
+    float32 arrays or CPU tensors (float32 or bfloat16; the call copies in and
+    out and synchronises)."""
     import torch
     if isinstance(z_coarsest, torch.Tensor):
+        dt, tdt = _emb_dtype(z_coarsest)
         d = z_coarsest.shape[1]
-        args = (_dev_ptr(z_coarsest, torch.float32, "z_coarsest"),
-                _dev_ptr(z_v_out, torch.float32, "z_v_out"),
-                _dev_ptr(z_e_out, torch.float32, "z_e_out"))
-        on_dev = 1
+        if z_coarsest.is_cuda:
+            args = (_dev_ptr(z_coarsest, tdt, "z_coarsest"), _dev_ptr(z_v_out, tdt, "z_v_out"),
+                    _dev_ptr(z_e_out, tdt, "z_e_out"))
+            on_dev = 1
+        else:
+            for a, nm in ((z_coarsest, "z_coarsest"), (z_v_out, "z_v_out"), (z_e_out, "z_e_out")):
+                if a.is_cuda or a.dtype != tdt or not a.is_contiguous():
+                    raise TypeError("%s must be a contiguous CPU %s tensor" % (nm, tdt))
+            args = (z_coarsest.data_ptr(), z_v_out.data_ptr(), z_e_out.data_ptr())
+            on_dev = 0
     else:
         for a, nm in ((z_coarsest, "z_coarsest"), (z_v_out, "z_v_out"), (z_e_out, "z_e_out")):
             if a.dtype != np.float32 or not a.flags.c_contiguous:
                 raise TypeError("%s must be a C-contiguous float32 array" % nm)
+        dt = F32
         d = z_coarsest.shape[1]
         args = (z_coarsest.ctypes.data, z_v_out.ctypes.data, z_e_out.ctypes.data)
         on_dev = 0
-    _check(lib().hnv_vcycle(g, *args, F32, int(d), float(omega), int(sweeps), int(mode), on_dev,
+    _check(lib().hnv_vcycle(g, *args, dt, int(d), float(omega), int(sweeps), int(mode), on_dev,
                             _stream_handle(stream)), "hnv_vcycle")
 
 

@@ -41,12 +41,20 @@ void destroy_graph(hnv_graph* g) {
 }
 
 int check_embedding_args(hnv_dtype dt, int d) {
-  if (dt == HNV_BF16) HNV_FAIL(HNV_ERR_UNSUPPORTED_D, "BF16 storage is not available in this build");
-  if (dt != HNV_F32) HNV_FAIL(HNV_ERR_INVALID_ARG, "unknown dtype %d", (int)dt);
-  if (d < 4 || d > 1024 || d % 4 != 0)
-    HNV_FAIL(HNV_ERR_UNSUPPORTED_D, "d = %d: need 4 <= d <= 1024 and d %% 4 == 0 for F32", d);
-  return HNV_OK;
+  if (dt == HNV_F32) {
+    if (d < 4 || d > 1024 || d % 4 != 0)
+      HNV_FAIL(HNV_ERR_UNSUPPORTED_D, "d = %d: need 4 <= d <= 1024 and d %% 4 == 0 for F32", d);
+    return HNV_OK;
+  }
+  if (dt == HNV_BF16) {
+    if (d < 8 || d > 1024 || d % 8 != 0)
+      HNV_FAIL(HNV_ERR_UNSUPPORTED_D, "d = %d: need 8 <= d <= 1024 and d %% 8 == 0 for BF16", d);
+    return HNV_OK;
+  }
+  HNV_FAIL(HNV_ERR_INVALID_ARG, "unknown dtype %d", (int)dt);
 }
+
+size_t dtype_size(hnv_dtype dt) { return dt == HNV_BF16 ? 2 : 4; }
 
 int check_buf(const void* p, int64_t rows, const char* name) {
   if (rows > 0 && p == nullptr) HNV_FAIL(HNV_ERR_INVALID_ARG, "%s is NULL", name);
@@ -70,40 +78,40 @@ void drop_maps(Level* lv, cudaStream_t s) {
   lv->rep_e = nullptr;
 }
 
-int vcycle_impl(hnv_graph* g, const float* z_coarsest, float* z_v_out, float* z_e_out, int d,
-                float omega, int sweeps, int mode, int on_device, cudaStream_t s) {
+int vcycle_impl(hnv_graph* g, const void* z_coarsest, void* z_v_out, void* z_e_out, int dtype,
+                int d, float omega, int sweeps, int mode, int on_device, cudaStream_t s) {
   const int L = (int)g->levels.size() - 1;
-  const size_t row_bytes = sizeof(float) * (size_t)d;
+  const size_t row_bytes = dtype_size((hnv_dtype)dtype) * (size_t)d;
   TempPool pool(s);
   size_t maxrows = 0;
   for (int l = 1; l <= L; ++l)
     maxrows = std::max(maxrows, (size_t)g->levels[l].n + (size_t)g->levels[l].m);
-  float* buf[2] = {nullptr, nullptr};
+  uint8_t* buf[2] = {nullptr, nullptr};
   if (L >= 1) {
-    HNV_CHECK(pool.get(&buf[0], maxrows * d));
-    HNV_CHECK(pool.get(&buf[1], maxrows * d));
+    HNV_CHECK(pool.get(&buf[0], maxrows * row_bytes));
+    HNV_CHECK(pool.get(&buf[1], maxrows * row_bytes));
   }
   const Level& l0 = g->levels[0];
-  float* out_v = z_v_out;
-  float* out_e = z_e_out;
+  uint8_t* out_v = static_cast<uint8_t*>(z_v_out);
+  uint8_t* out_e = static_cast<uint8_t*>(z_e_out);
   if (!on_device) {
-    HNV_CHECK(pool.get(&out_v, (size_t)l0.n * d));
-    HNV_CHECK(pool.get(&out_e, (size_t)l0.m * d));
+    HNV_CHECK(pool.get(&out_v, (size_t)l0.n * row_bytes));
+    HNV_CHECK(pool.get(&out_e, (size_t)l0.m * row_bytes));
   }
   auto zv = [&](int l) { return l == 0 ? out_v : buf[l & 1]; };
   auto ze = [&](int l) {
-    return l == 0 ? out_e : buf[l & 1] + (size_t)g->levels[l].n * d;
+    return l == 0 ? out_e : buf[l & 1] + (size_t)g->levels[l].n * row_bytes;
   };
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   const Level& top = g->levels[L];
-  if (top.n > 0)
-    HNV_CUDA(cudaMemcpyAsync(zv(L), z_coarsest, row_bytes * top.n, kind, s));
+  const uint8_t* zc = static_cast<const uint8_t*>(z_coarsest);
+  if (top.n > 0) HNV_CUDA(cudaMemcpyAsync(zv(L), zc, row_bytes * top.n, kind, s));
   if (top.m > 0)
-    HNV_CUDA(cudaMemcpyAsync(ze(L), z_coarsest + (size_t)top.n * d, row_bytes * top.m, kind, s));
-  HNV_CHECK(refine_level(g, L, zv(L), ze(L), d, omega, sweeps, mode, s));
+    HNV_CUDA(cudaMemcpyAsync(ze(L), zc + (size_t)top.n * row_bytes, row_bytes * top.m, kind, s));
+  HNV_CHECK(refine_level(g, L, zv(L), ze(L), dtype, d, omega, sweeps, mode, s));
   for (int l = L - 1; l >= 0; --l) {
-    HNV_CHECK(project_level(g, l, zv(l + 1), ze(l + 1), zv(l), ze(l), d, s));
-    HNV_CHECK(refine_level(g, l, zv(l), ze(l), d, omega, sweeps, mode, s));
+    HNV_CHECK(project_level(g, l, zv(l + 1), ze(l + 1), zv(l), ze(l), dtype, d, s));
+    HNV_CHECK(refine_level(g, l, zv(l), ze(l), dtype, d, omega, sweeps, mode, s));
   }
   if (!on_device) {
     if (l0.n > 0)
@@ -343,8 +351,8 @@ int hnv_project(const hnv_graph* g, int fine_level, const void* zc_v, const void
   HNV_CHECK(check_buf(zf_v, f.n, "zf_v"));
   HNV_CHECK(check_buf(zf_e, f.m, "zf_e"));
   DeviceGuard dgd(g->device);
-  return project_level(g, fine_level, (const float*)zc_v, (const float*)zc_e, (float*)zf_v,
-                       (float*)zf_e, d, reinterpret_cast<cudaStream_t>(stream));
+  return project_level(g, fine_level, zc_v, zc_e, zf_v, zf_e, (int)dt, d,
+                       reinterpret_cast<cudaStream_t>(stream));
 }
 
 int hnv_refine(hnv_graph* g, int level, void* z_v, void* z_e, hnv_dtype dt, int d, float omega,
@@ -362,7 +370,7 @@ int hnv_refine(hnv_graph* g, int level, void* z_v, void* z_e, hnv_dtype dt, int 
   HNV_CHECK(check_buf(z_v, lv.n, "z_v"));
   HNV_CHECK(check_buf(z_e, lv.m, "z_e"));
   DeviceGuard dgd(g->device);
-  return refine_level(g, level, (float*)z_v, (float*)z_e, d, omega, sweeps, (int)mode,
+  return refine_level(g, level, z_v, z_e, (int)dt, d, omega, sweeps, (int)mode,
                       reinterpret_cast<cudaStream_t>(stream));
 }
 
@@ -388,9 +396,8 @@ int hnv_vcycle(hnv_graph* g, const void* z_coarsest, void* z_v_out, void* z_e_ou
       HNV_FAIL(HNV_ERR_INVALID_ARG, "NULL host buffer");
   }
   DeviceGuard dgd(g->device);
-  return vcycle_impl(g, (const float*)z_coarsest, (float*)z_v_out, (float*)z_e_out, d, omega,
-                     sweeps_per_level, (int)mode, buffers_on_device,
-                     reinterpret_cast<cudaStream_t>(stream));
+  return vcycle_impl(g, z_coarsest, z_v_out, z_e_out, (int)dt, d, omega, sweeps_per_level,
+                     (int)mode, buffers_on_device, reinterpret_cast<cudaStream_t>(stream));
 }
 
 int hnv_sync_status(hnv_graph* g, hnv_stream_t stream) {

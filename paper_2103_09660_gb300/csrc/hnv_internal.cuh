@@ -227,10 +227,11 @@ int coarsen_step(hnv_graph* g, int level, const hnv_coarsen_params* p, const uin
                  Level* fine, Level* coarse);
 
 // refine.cu
-int refine_level(hnv_graph* g, int level, float* z_v, float* z_e, int d, float omega,
+// dtype: HNV_F32 or HNV_BF16 row storage (sums in float32 either way).
+int refine_level(hnv_graph* g, int level, void* z_v, void* z_e, int dtype, int d, float omega,
                  int sweeps, int mode, cudaStream_t s);
-int project_level(const hnv_graph* g, int fine_level, const float* zc_v, const float* zc_e,
-                  float* zf_v, float* zf_e, int d, cudaStream_t s);
+int project_level(const hnv_graph* g, int fine_level, const void* zc_v, const void* zc_e,
+                  void* zf_v, void* zf_e, int dtype, int d, cudaStream_t s);
 // tma_refine.cu: TMA-gather half-sweep for d in {32, 64, 128, 256}.
 bool tma_supported(int d);
 int tma_half_sweep(const SplitPlan& plan, const int32_t* idx, const float* inc_w,

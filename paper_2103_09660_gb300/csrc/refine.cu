@@ -20,6 +20,8 @@
 // deterministic, no atomics). A chunk writes its un-normalised partial sum;
 // finalize_kernel reduces a split row's partials in chunk order and applies
 // the relaxation.
+#include <cuda_bf16.h>
+
 #include <cstdlib>
 
 #include "hnv_internal.cuh"
@@ -30,34 +32,57 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 
-__device__ __forceinline__ float4 f4_zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+// A row is a sequence of 16-byte vectors: 4 float32 or 8 bfloat16 values.
+// Arithmetic is float32 either way; VecT converts a vector to and from its
+// float values (bfloat16 to float is exact; float to bfloat16 rounds to
+// nearest even on store).
+template <typename T>
+struct VecT;
 
-__device__ __forceinline__ void f4_add(float4& a, const float4& b) {
-  a.x += b.x;
-  a.y += b.y;
-  a.z += b.z;
-  a.w += b.w;
-}
+template <>
+struct VecT<float> {
+  static constexpr int N = 4;
+  __device__ __forceinline__ static void unpack(const uint4& v, float* f) {
+    f[0] = __uint_as_float(v.x);
+    f[1] = __uint_as_float(v.y);
+    f[2] = __uint_as_float(v.z);
+    f[3] = __uint_as_float(v.w);
+  }
+  __device__ __forceinline__ static uint4 pack(const float* f) {
+    return make_uint4(__float_as_uint(f[0]), __float_as_uint(f[1]), __float_as_uint(f[2]),
+                      __float_as_uint(f[3]));
+  }
+};
 
-__device__ __forceinline__ void f4_fma(float4& a, float s, const float4& b) {
-  a.x = fmaf(s, b.x, a.x);
-  a.y = fmaf(s, b.y, a.y);
-  a.z = fmaf(s, b.z, a.z);
-  a.w = fmaf(s, b.w, a.w);
-}
+template <>
+struct VecT<__nv_bfloat16> {
+  static constexpr int N = 8;
+  // each 32-bit word holds two values, the lower-indexed one in the low half
+  __device__ __forceinline__ static void unpack(const uint4& v, float* f) {
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      f[2 * k] = __uint_as_float(w[k] << 16);
+      f[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+    }
+  }
+  __device__ __forceinline__ static uint32_t pair(float lo, float hi) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&h);
+  }
+  __device__ __forceinline__ static uint4 pack(const float* f) {
+    return make_uint4(pair(f[0], f[1]), pair(f[2], f[3]), pair(f[4], f[5]), pair(f[6], f[7]));
+  }
+};
 
-// (1 - w) * self + (w * inv) * acc
-__device__ __forceinline__ float4 relax4(float keep, float sc, const float4& self, const float4& acc) {
-  return make_float4(fmaf(keep, self.x, sc * acc.x), fmaf(keep, self.y, sc * acc.y),
-                     fmaf(keep, self.z, sc * acc.z), fmaf(keep, self.w, sc * acc.w));
-}
-
-template <int G, int VPL, bool WEIGHTED>
+template <typename T, int G, int VPL, bool WEIGHTED>
 __global__ void __launch_bounds__(256)
 gather_kernel(const int4* __restrict__ items, int32_t n_items, const int32_t* __restrict__ idx,
               const float* __restrict__ inc_w, const float* __restrict__ inv_norm,
-              const float4* __restrict__ src, const float4* self_in, float4* out, int32_t d4,
-              float omega, float4* __restrict__ partials) {
+              const uint4* __restrict__ src, const uint4* self_in, uint4* out, int32_t dv,
+              float omega, float* __restrict__ partials) {
+  using V = VecT<T>;
+  constexpr int N = V::N;
   constexpr int R = 32 / G;                                    // items per warp pass
   // row loads in flight per lane (the weighted variant also holds a weight
   // per load, so it takes half as many to keep its register count down)
@@ -69,6 +94,7 @@ gather_kernel(const int4* __restrict__ items, int32_t n_items, const int32_t* __
   const int lg = lane & (G - 1);
   const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
   const float keep = 1.0f - omega;
+  const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
 
   for (int64_t wbase = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * R;
        wbase < n_items; wbase += warps_total * R) {
@@ -78,17 +104,19 @@ gather_kernel(const int4* __restrict__ items, int32_t n_items, const int32_t* __
     const int32_t row = it.x, beg = it.y, len = it.z, slot = it.w;
     const bool is_row = (row >= 0) && (slot < 0);
 
-    float4 sv[VPL];
+    uint4 sv[VPL];
     if (is_row) {
 #pragma unroll
       for (int j = 0; j < VPL; ++j) {
         const int col = lg + j * G;
-        sv[j] = (col < d4) ? self_in[(size_t)row * d4 + col] : f4_zero();
+        sv[j] = (col < dv) ? self_in[(size_t)row * dv + col] : zero4;
       }
     }
-    float4 acc[VPL];
+    float acc[VPL][N];
 #pragma unroll
-    for (int j = 0; j < VPL; ++j) acc[j] = f4_zero();
+    for (int j = 0; j < VPL; ++j)
+#pragma unroll
+      for (int e = 0; e < N; ++e) acc[j][e] = 0.f;
 
     const int32_t maxlen = __reduce_max_sync(FULL, len);
     for (int32_t off = 0; off < maxlen; off += G) {
@@ -99,7 +127,7 @@ gather_kernel(const int4* __restrict__ items, int32_t n_items, const int32_t* __
       if (WEIGHTED) my_w = have ? __ldg(inc_w + beg + off + lg) : 0.f;
       const int32_t cnt = min(G, maxlen - off);
       for (int32_t t = 0; t < cnt; t += U) {
-        float4 x[U][VPL];
+        uint4 x[U][VPL];
         float wt[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -107,11 +135,11 @@ gather_kernel(const int4* __restrict__ items, int32_t n_items, const int32_t* __
           const int32_t nb = __shfl_sync(FULL, my_idx, sl, G);
           const bool ok = (t + u) < mine;
           wt[u] = WEIGHTED ? (ok ? __shfl_sync(FULL, my_w, sl, G) : 0.f) : 1.f;
-          const float4* rowp = src + (size_t)nb * d4;
+          const uint4* rowp = src + (size_t)nb * dv;
 #pragma unroll
           for (int j = 0; j < VPL; ++j) {
             const int col = lg + j * G;
-            x[u][j] = (ok && col < d4) ? __ldg(rowp + col) : f4_zero();
+            x[u][j] = (ok && col < dv) ? __ldg(rowp + col) : zero4;
           }
         }
         // invalid slots loaded zeros (and weight 0): adding them is exact
@@ -119,10 +147,15 @@ gather_kernel(const int4* __restrict__ items, int32_t n_items, const int32_t* __
         for (int u = 0; u < U; ++u) {
 #pragma unroll
           for (int j = 0; j < VPL; ++j) {
-            if (WEIGHTED)
-              f4_fma(acc[j], wt[u], x[u][j]);
-            else
-              f4_add(acc[j], x[u][j]);
+            float xf[N];
+            V::unpack(x[u][j], xf);
+#pragma unroll
+            for (int e = 0; e < N; ++e) {
+              if (WEIGHTED)
+                acc[j][e] = fmaf(wt[u], xf[e], acc[j][e]);
+              else
+                acc[j][e] += xf[e];
+            }
           }
         }
       }
@@ -133,13 +166,25 @@ gather_kernel(const int4* __restrict__ items, int32_t n_items, const int32_t* __
 #pragma unroll
       for (int j = 0; j < VPL; ++j) {
         const int col = lg + j * G;
-        if (col < d4) out[(size_t)row * d4 + col] = relax4(keep, sc, sv[j], acc[j]);
+        if (col < dv) {
+          float sf[N], r[N];
+          V::unpack(sv[j], sf);
+#pragma unroll
+          for (int e = 0; e < N; ++e) r[e] = fmaf(keep, sf[e], sc * acc[j][e]);
+          out[(size_t)row * dv + col] = V::pack(r);
+        }
       }
     } else if (slot >= 0) {
 #pragma unroll
       for (int j = 0; j < VPL; ++j) {
         const int col = lg + j * G;
-        if (col < d4) partials[(size_t)slot * d4 + col] = acc[j];
+        if (col < dv) {
+          float4* pp = reinterpret_cast<float4*>(partials + ((size_t)slot * dv + col) * N);
+#pragma unroll
+          for (int q = 0; q < N / 4; ++q)
+            pp[q] = make_float4(acc[j][4 * q], acc[j][4 * q + 1], acc[j][4 * q + 2],
+                                acc[j][4 * q + 3]);
+        }
       }
     }
   }
@@ -147,15 +192,23 @@ gather_kernel(const int4* __restrict__ items, int32_t n_items, const int32_t* __
 
 // Reduces the chunk partials of split rows in chunk order and relaxes.
 // Blocks [0, mid_blocks) give one warp to each of the first n_mid rows (at
-// most kMidChunks chunks: lanes over columns, four interleaved
+// most kMidChunks chunks: lanes over row vectors, four interleaved
 // accumulators); each later block takes one of the n_huge rows: S =
-// blockDim / d4 slices sum contiguous runs of chunks (four interleaved
+// blockDim / dv slices sum contiguous runs of chunks (four interleaved
 // accumulators each) and slice 0 adds the slices in order.
 constexpr int kFinThreads = 1024;
 
+__device__ __forceinline__ void f4_add(float4& a, const float4& b) {
+  a.x += b.x;
+  a.y += b.y;
+  a.z += b.z;
+  a.w += b.w;
+}
+
+// Sum of count float4 values p[0], p[stride], p[2*stride], ... (fixed order).
 __device__ __forceinline__ float4 sum_strided4(const float4* __restrict__ p, int32_t count,
                                                int32_t stride) {
-  float4 a0 = f4_zero(), a1 = f4_zero(), a2 = f4_zero(), a3 = f4_zero();
+  float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, a2 = a0, a3 = a0;
   int32_t c = 0;
   for (; c + 4 <= count; c += 4) {
     const float4 p0 = p[(size_t)c * stride];
@@ -174,12 +227,31 @@ __device__ __forceinline__ float4 sum_strided4(const float4* __restrict__ p, int
   return a0;
 }
 
+// Sum over `count` chunks of one row vector's N partial floats.
+template <int N>
+__device__ __forceinline__ void sum_chunks(const float* __restrict__ partials, int32_t first,
+                                           int32_t count, int32_t dv, int32_t col, float* out) {
+  const float4* base = reinterpret_cast<const float4*>(partials) + ((size_t)first * dv + col) * (N / 4);
+#pragma unroll
+  for (int q = 0; q < N / 4; ++q) {
+    const float4 t = sum_strided4(base + q, count, dv * (N / 4));
+    out[4 * q] = t.x;
+    out[4 * q + 1] = t.y;
+    out[4 * q + 2] = t.z;
+    out[4 * q + 3] = t.w;
+  }
+}
+
+template <typename T>
 __global__ void __launch_bounds__(kFinThreads)
 finalize_kernel(const int4* __restrict__ long_desc, int32_t n_mid, int32_t n_huge,
-                int32_t mid_blocks, const float4* __restrict__ partials,
-                const float* __restrict__ inv_norm, const float4* self_in, float4* out,
-                int32_t d4, float omega) {
-  extern __shared__ float4 sm[];
+                int32_t mid_blocks, const float* __restrict__ partials,
+                const float* __restrict__ inv_norm, const uint4* self_in, uint4* out,
+                int32_t dv, float omega) {
+  using V = VecT<T>;
+  constexpr int N = V::N;
+  extern __shared__ float4 sm4[];
+  float* sm = reinterpret_cast<float*>(sm4);
   const float keep = 1.0f - omega;
   if ((int32_t)blockIdx.x < mid_blocks) {
     const int32_t k = blockIdx.x * (kFinThreads / 32) + (threadIdx.x >> 5);
@@ -187,64 +259,80 @@ finalize_kernel(const int4* __restrict__ long_desc, int32_t n_mid, int32_t n_hug
     const int4 ds = long_desc[k];
     const int lane = threadIdx.x & 31;
     const float sc = omega * inv_norm[ds.x];
-    for (int col = lane; col < d4; col += 32) {
-      const float4 tot = sum_strided4(partials + (size_t)ds.y * d4 + col, ds.z, d4);
-      const size_t o = (size_t)ds.x * d4 + col;
-      out[o] = relax4(keep, sc, self_in[o], tot);
+    for (int col = lane; col < dv; col += 32) {
+      float tot[N], sf[N], r[N];
+      sum_chunks<N>(partials, ds.y, ds.z, dv, col, tot);
+      const size_t o = (size_t)ds.x * dv + col;
+      V::unpack(self_in[o], sf);
+#pragma unroll
+      for (int e = 0; e < N; ++e) r[e] = fmaf(keep, sf[e], sc * tot[e]);
+      out[o] = V::pack(r);
     }
     return;
   }
   const int32_t k = n_mid + (int32_t)blockIdx.x - mid_blocks;
   if (k >= n_mid + n_huge) return;
   const int4 ds = long_desc[k];
-  const int S = (int)blockDim.x / d4;
+  const int S = (int)blockDim.x / dv;
   const int t = threadIdx.x;
-  const int slice = t / d4;
-  const int col = t - slice * d4;
+  const int slice = t / dv;
+  const int col = t - slice * dv;
   if (slice < S) {
     const int32_t a = (int32_t)((int64_t)ds.z * slice / S);
     const int32_t b = (int32_t)((int64_t)ds.z * (slice + 1) / S);
-    sm[slice * d4 + col] = sum_strided4(partials + (size_t)(ds.y + a) * d4 + col, b - a, d4);
+    float part[N];
+    sum_chunks<N>(partials, ds.y + a, b - a, dv, col, part);
+#pragma unroll
+    for (int e = 0; e < N; ++e) sm[((size_t)slice * dv + col) * N + e] = part[e];
   }
   __syncthreads();
   if (slice == 0) {
-    float4 tot = sm[col];
-    for (int q = 1; q < S; ++q) f4_add(tot, sm[q * d4 + col]);
-    const size_t o = (size_t)ds.x * d4 + col;
-    out[o] = relax4(keep, omega * inv_norm[ds.x], self_in[o], tot);
+    float tot[N], sf[N], r[N];
+#pragma unroll
+    for (int e = 0; e < N; ++e) tot[e] = sm[(size_t)col * N + e];
+    for (int q = 1; q < S; ++q)
+#pragma unroll
+      for (int e = 0; e < N; ++e) tot[e] += sm[((size_t)q * dv + col) * N + e];
+    const size_t o = (size_t)ds.x * dv + col;
+    V::unpack(self_in[o], sf);
+    const float sc = omega * inv_norm[ds.x];
+#pragma unroll
+    for (int e = 0; e < N; ++e) r[e] = fmaf(keep, sf[e], sc * tot[e]);
+    out[o] = V::pack(r);
   }
 }
 
 // Out-of-place sweeps (Jacobi): rows without neighbours carry over.
 __global__ void copy_rows_kernel(const int32_t* __restrict__ rows, int32_t n_rows,
-                                 const float4* __restrict__ src, float4* __restrict__ dst,
-                                 int32_t d4) {
-  const int64_t total = (int64_t)n_rows * d4;
+                                 const uint4* __restrict__ src, uint4* __restrict__ dst,
+                                 int32_t dv) {
+  const int64_t total = (int64_t)n_rows * dv;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t k = i / d4;
-    const int32_t col = (int32_t)(i - k * d4);
-    const size_t o = (size_t)rows[k] * d4 + col;
+    const int64_t k = i / dv;
+    const int32_t col = (int32_t)(i - k * dv);
+    const size_t o = (size_t)rows[k] * dv + col;
     dst[o] = src[o];
   }
 }
 
+// Projection: bitwise row copies through rep_v / rep_e (any element type).
 __global__ void project_kernel(int32_t n, int32_t m, const int32_t* __restrict__ rep_v,
-                               const int32_t* __restrict__ rep_e, const float4* __restrict__ zc_v,
-                               const float4* __restrict__ zc_e, float4* __restrict__ zf_v,
-                               float4* __restrict__ zf_e, int32_t d4) {
-  const int64_t total = ((int64_t)n + m) * d4;
+                               const int32_t* __restrict__ rep_e, const uint4* __restrict__ zc_v,
+                               const uint4* __restrict__ zc_e, uint4* __restrict__ zf_v,
+                               uint4* __restrict__ zf_e, int32_t dv) {
+  const int64_t total = ((int64_t)n + m) * dv;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t row = i / d4;
-    const int32_t col = (int32_t)(i - row * d4);
+    const int64_t row = i / dv;
+    const int32_t col = (int32_t)(i - row * dv);
     if (row < n) {
-      zf_v[i] = zc_v[(size_t)rep_v[row] * d4 + col];
+      zf_v[i] = zc_v[(size_t)rep_v[row] * dv + col];
     } else {
       const int64_t e = row - n;
       const int32_t r = rep_e[e];
-      const float4* s = (r >= 0) ? zc_e + (size_t)r * d4 : zc_v + (size_t)(-1 - r) * d4;
-      zf_e[e * d4 + col] = s[col];
+      const uint4* s = (r >= 0) ? zc_e + (size_t)r * dv : zc_v + (size_t)(-1 - r) * dv;
+      zf_e[e * dv + col] = s[col];
     }
   }
 }
@@ -265,9 +353,10 @@ struct HalfSweep {
 
 // Which gather path the half-sweeps use. The default is the per-lane load
 // path (gather_kernel). HNV_GATHER=tma selects the TMA-gather path
-// (tma_refine.cu) where it has a variant for d; both compute the same sums.
-// Measured on the 1M-node workload the TMA path is slower (per-row tensor
-// copies of 512-byte rows cap its throughput), so it is opt-in.
+// (tma_refine.cu) for float32 rows where it has a variant for d; both
+// compute the same sums. Measured on the 1M-node workload the TMA path is
+// slower (per-row tensor copies of 512-byte rows cap its throughput), so it
+// is opt-in.
 bool use_tma(int d) {
   static int mode = -1;
   if (mode < 0) {
@@ -277,9 +366,9 @@ bool use_tma(int d) {
   return mode == 1 && tma_supported(d);
 }
 
-template <int G, int VPL>
-int launch_items(const HalfSweep& h, const int4* items, int32_t n_items, const float* src,
-                 const float* self_in, float* out, int d4, float omega, float* partials,
+template <typename T, int G, int VPL>
+int launch_items(const HalfSweep& h, const int4* items, int32_t n_items, const void* src,
+                 const void* self_in, void* out, int dv, float omega, float* partials,
                  cudaStream_t s) {
   if (n_items <= 0) return HNV_OK;
   constexpr int R = 32 / G;
@@ -287,20 +376,21 @@ int launch_items(const HalfSweep& h, const int4* items, int32_t n_items, const f
   const int64_t blocks64 = (warps + 7) / 8;
   const unsigned blocks = (unsigned)(blocks64 > 0x7fffffff ? 0x7fffffff : blocks64);
   if (h.inc_w)
-    return launch("gather_w", gather_kernel<G, VPL, true>, blocks, 256, 0, s, items, n_items,
-                  h.idx, h.inc_w, h.inv_norm, (const float4*)src, (const float4*)self_in,
-                  (float4*)out, d4, omega, (float4*)partials);
-  return launch("gather", gather_kernel<G, VPL, false>, blocks, 256, 0, s, items, n_items, h.idx,
-                h.inc_w, h.inv_norm, (const float4*)src, (const float4*)self_in, (float4*)out,
-                d4, omega, (float4*)partials);
+    return launch("gather_w", gather_kernel<T, G, VPL, true>, blocks, 256, 0, s, items, n_items,
+                  h.idx, h.inc_w, h.inv_norm, (const uint4*)src, (const uint4*)self_in,
+                  (uint4*)out, dv, omega, partials);
+  return launch("gather", gather_kernel<T, G, VPL, false>, blocks, 256, 0, s, items, n_items,
+                h.idx, h.inc_w, h.inv_norm, (const uint4*)src, (const uint4*)self_in, (uint4*)out,
+                dv, omega, partials);
 }
 
+template <typename T>
 int launch_items_dispatch(int G, int VPL, const HalfSweep& h, const int4* items, int32_t n_items,
-                          const float* src, const float* self_in, float* out, int d4,
-                          float omega, float* partials, cudaStream_t s) {
-#define HNV_CASE(g, v)                                                                 \
-  if (G == g && VPL == v)                                                              \
-    return launch_items<g, v>(h, items, n_items, src, self_in, out, d4, omega, partials, s);
+                          const void* src, const void* self_in, void* out, int dv, float omega,
+                          float* partials, cudaStream_t s) {
+#define HNV_CASE(g, v)                                                                     \
+  if (G == g && VPL == v)                                                                  \
+    return launch_items<T, g, v>(h, items, n_items, src, self_in, out, dv, omega, partials, s);
   HNV_CASE(1, 1) HNV_CASE(2, 1) HNV_CASE(4, 1)
   HNV_CASE(8, 1) HNV_CASE(8, 2) HNV_CASE(8, 4) HNV_CASE(8, 8)
   HNV_CASE(16, 1) HNV_CASE(16, 2) HNV_CASE(16, 4) HNV_CASE(16, 8)
@@ -316,51 +406,63 @@ int next_pow2(int x) {
 }
 
 // Lanes per item for a class whose natural width is `cls` lanes: at most the
-// row width in float4s (rounded up to a power of two), at least enough that
-// a lane holds no more than 8 float4s.
-int group_lanes(int cls, int d4) {
-  int g = cls < next_pow2(d4) ? cls : next_pow2(d4);
-  const int gmin = next_pow2((d4 + 7) / 8);
+// row width in vectors (rounded up to a power of two), at least enough that
+// a lane holds no more than 8 vectors.
+int group_lanes(int cls, int dv) {
+  int g = cls < next_pow2(dv) ? cls : next_pow2(dv);
+  const int gmin = next_pow2((dv + 7) / 8);
   if (g < gmin) g = gmin;
   return g > 32 ? 32 : g;
 }
 
-int run_half_dispatch(const HalfSweep& h, const float* src, const float* self_in, float* out,
-                      int d, float omega, float* partials, cudaStream_t s) {
-  const int d4 = d / 4;
-  if (d4 < 1 || d4 > 256) HNV_FAIL(HNV_ERR_UNSUPPORTED_D, "d = %d not in [4, 1024]", d);
+template <typename T>
+int run_half(const HalfSweep& h, const void* src, const void* self_in, void* out, int d,
+             float omega, float* partials, cudaStream_t s) {
+  constexpr int N = VecT<T>::N;
+  const int dv = d / N;
+  if (dv < 1 || dv > 256) HNV_FAIL(HNV_ERR_UNSUPPORTED_D, "d = %d out of range", d);
   const SplitPlan& p = *h.plan;
-  if (use_tma(d)) {
-    HNV_CHECK(tma_half_sweep(p, h.idx, h.inc_w, h.inv_norm, src, h.src_rows, self_in, out,
-                             h.self_rows, d, omega, partials, h.err, s));
+  if (sizeof(T) == 4 && use_tma(d)) {
+    HNV_CHECK(tma_half_sweep(p, h.idx, h.inc_w, h.inv_norm, (const float*)src, h.src_rows,
+                             (const float*)self_in, (float*)out, h.self_rows, d, omega, partials,
+                             h.err, s));
   } else {
     const int4* items = p.items;
     const int cls_lanes[3] = {8, 16, 32};
     const int32_t counts[3] = {p.n_a, p.n_b, p.n_c + p.n_d + p.n_chunks};
     int32_t off = 0;
     for (int c = 0; c < 3; ++c) {
-      const int G = group_lanes(cls_lanes[c], d4);
-      const int VPL = next_pow2((d4 + G - 1) / G);
-      HNV_CHECK(launch_items_dispatch(G, VPL, h, items + off, counts[c], src, self_in, out, d4,
-                                      omega, partials, s));
+      const int G = group_lanes(cls_lanes[c], dv);
+      const int VPL = next_pow2((dv + G - 1) / G);
+      HNV_CHECK(launch_items_dispatch<T>(G, VPL, h, items + off, counts[c], src, self_in, out, dv,
+                                         omega, partials, s));
       off += counts[c];
     }
   }
   if (p.n_mid + p.n_huge > 0) {
     const int32_t mid_blocks = (p.n_mid + kFinThreads / 32 - 1) / (kFinThreads / 32);
-    const int S = kFinThreads / d4;
-    const size_t smem = sizeof(float4) * (size_t)S * d4;
-    HNV_CHECK(launch("finalize", finalize_kernel, (unsigned)(mid_blocks + p.n_huge), kFinThreads,
-                     smem, s, (const int4*)p.long_desc, p.n_mid, p.n_huge, mid_blocks,
-                     (const float4*)partials, h.inv_norm, (const float4*)self_in, (float4*)out,
-                     d4, omega));
+    const int S = kFinThreads / dv;
+    const size_t smem = sizeof(float) * (size_t)S * dv * N;
+    HNV_CHECK(launch("finalize", finalize_kernel<T>, (unsigned)(mid_blocks + p.n_huge),
+                     kFinThreads, smem, s, (const int4*)p.long_desc, p.n_mid, p.n_huge,
+                     mid_blocks, (const float*)partials, h.inv_norm, (const uint4*)self_in,
+                     (uint4*)out, dv, omega));
   }
   if (self_in != out && p.n_zero > 0)
-    HNV_CHECK(launch("copy_rows", copy_rows_kernel, grid_for((int64_t)p.n_zero * d4, 256), 256, 0,
-                     s, (const int32_t*)p.zero_rows, p.n_zero, (const float4*)self_in,
-                     (float4*)out, d4));
+    HNV_CHECK(launch("copy_rows", copy_rows_kernel, grid_for((int64_t)p.n_zero * dv, 256), 256, 0,
+                     s, (const int32_t*)p.zero_rows, p.n_zero, (const uint4*)self_in,
+                     (uint4*)out, dv));
   return HNV_OK;
 }
+
+int run_half_dispatch(const HalfSweep& h, const void* src, const void* self_in, void* out,
+                      int dtype, int d, float omega, float* partials, cudaStream_t s) {
+  if (dtype == HNV_BF16)
+    return run_half<__nv_bfloat16>(h, src, self_in, out, d, omega, partials, s);
+  return run_half<float>(h, src, self_in, out, d, omega, partials, s);
+}
+
+size_t elem_size(int dtype) { return dtype == HNV_BF16 ? 2 : 4; }
 
 int ensure_scratch(float** p, size_t* have, size_t need, cudaStream_t s) {
   if (need <= *have && *p) return HNV_OK;
@@ -376,41 +478,42 @@ int ensure_scratch(float** p, size_t* have, size_t need, cudaStream_t s) {
 
 }  // namespace
 
-int refine_level(hnv_graph* g, int level, float* z_v, float* z_e, int d, float omega, int sweeps,
-                 int mode, cudaStream_t s) {
+int refine_level(hnv_graph* g, int level, void* z_v, void* z_e, int dtype, int d, float omega,
+                 int sweeps, int mode, cudaStream_t s) {
   Level& lv = g->levels[level];
   const int64_t chunks = lv.planE.n_chunks > lv.planV.n_chunks ? lv.planE.n_chunks : lv.planV.n_chunks;
   HNV_CHECK(ensure_scratch(&g->partials, &g->partials_bytes,
                            sizeof(float) * (size_t)(chunks > 0 ? chunks : 1) * d, s));
+  const size_t es = elem_size(dtype);
   if (mode == HNV_SWEEP_JACOBI)
     HNV_CHECK(ensure_scratch(&g->jacobi_tmp, &g->jacobi_bytes,
-                             sizeof(float) * ((size_t)lv.m > 0 ? lv.m : 1) * d, s));
+                             es * ((size_t)lv.m > 0 ? lv.m : 1) * d, s));
   const HalfSweep E{lv.e_nodes, nullptr, lv.inv_size_e, &lv.planE, lv.n, lv.m, g->d_err};
   const HalfSweep V{lv.v_edges, lv.v_w, lv.inv_deg_v, &lv.planV, lv.m, lv.n, g->d_err};
   const double n = lv.n, m = lv.m, nnz = (double)lv.nnz;
-  const double bytesE = 4.0 * (n * d + 2.0 * m * d + nnz + 2.0 * m + 1.0);
-  const double bytesV = 4.0 * (m * d + 2.0 * n * d + 2.0 * nnz + 2.0 * n + 1.0);
+  const double bytesE = (double)es * (n * d + 2.0 * m * d) + 4.0 * (nnz + 2.0 * m + 1.0);
+  const double bytesV = (double)es * (m * d + 2.0 * n * d) + 4.0 * (2.0 * nnz + 2.0 * n + 1.0);
   for (int it = 0; it < sweeps; ++it) {
     if (mode == HNV_SWEEP_TWO_PHASE) {
       {
         PhaseScope ps(HNV_PHASE_REFINE_E, s, bytesE);
-        HNV_CHECK(run_half_dispatch(E, z_v, z_e, z_e, d, omega, g->partials, s));
+        HNV_CHECK(run_half_dispatch(E, z_v, z_e, z_e, dtype, d, omega, g->partials, s));
       }
       {
         PhaseScope ps(HNV_PHASE_REFINE_V, s, bytesV);
-        HNV_CHECK(run_half_dispatch(V, z_e, z_v, z_v, d, omega, g->partials, s));
+        HNV_CHECK(run_half_dispatch(V, z_e, z_v, z_v, dtype, d, omega, g->partials, s));
       }
     } else {
       {
         PhaseScope ps(HNV_PHASE_REFINE_E, s, bytesE);
-        HNV_CHECK(run_half_dispatch(E, z_v, z_e, g->jacobi_tmp, d, omega, g->partials, s));
+        HNV_CHECK(run_half_dispatch(E, z_v, z_e, g->jacobi_tmp, dtype, d, omega, g->partials, s));
       }
       {
         PhaseScope ps(HNV_PHASE_REFINE_V, s, bytesV);
-        HNV_CHECK(run_half_dispatch(V, z_e, z_v, z_v, d, omega, g->partials, s));
+        HNV_CHECK(run_half_dispatch(V, z_e, z_v, z_v, dtype, d, omega, g->partials, s));
       }
       if (lv.m > 0)
-        HNV_CUDA(cudaMemcpyAsync(z_e, g->jacobi_tmp, sizeof(float) * (size_t)lv.m * d,
+        HNV_CUDA(cudaMemcpyAsync(z_e, g->jacobi_tmp, es * (size_t)lv.m * d,
                                  cudaMemcpyDeviceToDevice, s));
     }
   }
@@ -423,24 +526,25 @@ int refine_two_phase_with_partials(const hnv_graph* g, int level, float* z_v, fl
   const HalfSweep E{lv.e_nodes, nullptr, lv.inv_size_e, &lv.planE, lv.n, lv.m, g->d_err};
   const HalfSweep V{lv.v_edges, lv.v_w, lv.inv_deg_v, &lv.planV, lv.m, lv.n, g->d_err};
   for (int it = 0; it < sweeps; ++it) {
-    HNV_CHECK(run_half_dispatch(E, z_v, z_e, z_e, d, omega, partials, s));
-    HNV_CHECK(run_half_dispatch(V, z_e, z_v, z_v, d, omega, partials, s));
+    HNV_CHECK(run_half_dispatch(E, z_v, z_e, z_e, HNV_F32, d, omega, partials, s));
+    HNV_CHECK(run_half_dispatch(V, z_e, z_v, z_v, HNV_F32, d, omega, partials, s));
   }
   return HNV_OK;
 }
 
-int project_level(const hnv_graph* g, int fine_level, const float* zc_v, const float* zc_e,
-                  float* zf_v, float* zf_e, int d, cudaStream_t s) {
+int project_level(const hnv_graph* g, int fine_level, const void* zc_v, const void* zc_e,
+                  void* zf_v, void* zf_e, int dtype, int d, cudaStream_t s) {
   const Level& f = g->levels[fine_level];
   const Level& c = g->levels[fine_level + 1];
-  const int d4 = d / 4;
-  const double bytes = 4.0 * (((double)f.n + f.m) * d * 1.0 + ((double)c.n + c.m) * d +
-                              (double)f.n + f.m);
+  const size_t es = elem_size(dtype);
+  const int dv = (int)(d * es / 16);
+  const double bytes = (double)es * (((double)f.n + f.m) * d + ((double)c.n + c.m) * d) +
+                       4.0 * ((double)f.n + f.m);
   PhaseScope ps(HNV_PHASE_PROJECT, s, bytes);
-  const int64_t total = ((int64_t)f.n + f.m) * d4;
+  const int64_t total = ((int64_t)f.n + f.m) * dv;
   return launch("project", project_kernel, grid_for(total, 256, 16), 256, 0, s, f.n, f.m,
-                (const int32_t*)f.rep_v, (const int32_t*)f.rep_e, (const float4*)zc_v,
-                (const float4*)zc_e, (float4*)zf_v, (float4*)zf_e, d4);
+                (const int32_t*)f.rep_v, (const int32_t*)f.rep_e, (const uint4*)zc_v,
+                (const uint4*)zc_e, (uint4*)zf_v, (uint4*)zf_e, dv);
 }
 
 }  // namespace hnv

@@ -317,8 +317,8 @@ def test_error_codes(H):
             G.project(0, zv, ze, zv, ze)                    # no coarse level yet
         assert ei.value.code == -2
         L = H.lib()
-        assert L.hnv_refine(G.handle, 0, zv.data_ptr(), ze.data_ptr(), H.BF16, 8, 0.5, 1, 0,
-                            None) == -7                     # BF16 not in this build
+        assert L.hnv_refine(G.handle, 0, zv.data_ptr(), ze.data_ptr(), H.BF16, 12, 0.5, 1, 0,
+                            None) == -7                     # BF16 needs d % 8 == 0
         assert L.hnv_refine(G.handle, 0, zv.data_ptr() + 4, ze.data_ptr(), H.F32, 8, 0.5, 1, 0,
                             None) == -1                     # misaligned
     # the context is still usable after the reported errors
