@@ -475,3 +475,108 @@ def vcycle(h: Hierarchy, z_coarsest: np.ndarray, omega: float, sweeps: int,
         if keep_levels:
             per[ell] = (z_v, z_e)
     return VCycleResult(z_v=z_v, z_e=z_e, per_level=per)
+
+
+# ---------------------------------------------------------------------------
+# Reverse mode (adjoint) of the two-phase V-cycle
+# ---------------------------------------------------------------------------
+#
+# The forward map is (w0, Z^L) -> (Z_V^0, Z_E^0): the level-l weights are the
+# level-0 weights of the hyperedges they came from, w_l = w0[orig_e_l], and
+# enter the node half-sweeps through the weighted mean
+#   z~_v = s_v / D_v,   s_v = sum_{e ∋ v} w_e z_e,   D_v = sum_{e ∋ v} w_e,
+# so d z~_v / d w_e = (z_e - z~_v) / D_v. Reverse mode follows the sweeps
+# backwards; every step is the transpose of the forward step.
+
+def with_weights(h: Hierarchy, w0: np.ndarray) -> Hierarchy:
+    """The same hierarchy with level-0 weights `w0` (float64) propagated to
+    every level through orig_e (coarse hyperedges keep their weight)."""
+    w0 = np.asarray(w0, dtype=np.float64)
+    levels = []
+    for lv in h.levels:
+        w = w0[lv.orig_e]
+        levels.append(dataclasses.replace(lv, w=w, w32=w.astype(np.float32)))
+    return Hierarchy(levels=levels, rep_v=h.rep_v, rep_e=h.rep_e)
+
+
+def refine_states(lv: Level, z_v: np.ndarray, z_e: np.ndarray, omega: float, sweeps: int):
+    """Two-phase refinement keeping every iterate: [(z_v^0, z_e^0), ...,
+    (z_v^k, z_e^k)]."""
+    states = [(np.array(z_v, dtype=np.float64), np.array(z_e, dtype=np.float64))]
+    for _ in range(sweeps):
+        states.append(refine(lv, states[-1][0], states[-1][1], omega, 1, SWEEP_TWO_PHASE))
+    return states
+
+
+def refine_backward(lv: Level, states, omega: float, g_v: np.ndarray, g_e: np.ndarray):
+    """Adjoint of two-phase `refine`: from dL/d(z_v^k, z_e^k) to
+    dL/d(z_v^0, z_e^0) and dL/dw (this level's weights)."""
+    He, Hv = incidence_matrices(lv)
+    size = lv.size_e().astype(np.float64)
+    deg = lv.deg_v()
+    has_v = np.diff(lv.v_ptr) > 0
+    has_e = size > 0
+    g_v = np.array(g_v, dtype=np.float64)
+    g_e = np.array(g_e, dtype=np.float64)
+    dw = np.zeros(lv.m)
+    for i in range(len(states) - 1, 0, -1):
+        _, ze_i = states[i]
+        zv_prev, _ = states[i - 1]
+        # node half-sweep of sweep i: z_v^i = (1-w) z_v^{i-1} + w s_v / D_v
+        zt_v, _ = smooth_nodes(lv, Hv, deg, ze_i)
+        a = np.zeros_like(g_v)
+        a[has_v] = g_v[has_v] / deg[has_v, None]
+        A = He @ a                                         # sum_{v in e} a_v
+        c = np.einsum("ij,ij->i", a, zt_v)                 # <a_v, z~_v>
+        dw += omega * (np.einsum("ij,ij->i", A, ze_i) - He @ c)
+        g_e = g_e + omega * lv.w[:, None] * A
+        g_v[has_v] *= (1.0 - omega)
+        # hyperedge half-sweep of sweep i: z_e^i = (1-w) z_e^{i-1} + w mean_{v in e} z_v^{i-1}
+        b = np.zeros_like(g_e)
+        b[has_e] = g_e[has_e] / size[has_e, None]
+        g_v = g_v + omega * (He.T @ b)
+        g_e[has_e] *= (1.0 - omega)
+    return g_v, g_e, dw
+
+
+def project_backward(rep_v: np.ndarray, rep_e: np.ndarray, n_c: int, m_c: int,
+                     gf_v: np.ndarray, gf_e: np.ndarray):
+    """Adjoint of `project`: a coarse row collects the gradients of every fine
+    row copied from it."""
+    d = gf_v.shape[1]
+    gc_v = np.zeros((n_c, d))
+    gc_e = np.zeros((m_c, d))
+    np.add.at(gc_v, rep_v, gf_v)
+    kept = rep_e >= 0
+    np.add.at(gc_e, rep_e[kept], gf_e[kept])
+    np.add.at(gc_v, -1 - rep_e[~kept], gf_e[~kept])
+    return gc_v, gc_e
+
+
+def vcycle_grad(h: Hierarchy, z_coarsest: np.ndarray, omega: float, sweeps: int,
+                g_v0: np.ndarray, g_e0: np.ndarray):
+    """dL/dw0 and dL/dZ^L of the two-phase V-cycle, given dL/dZ_V^0 and
+    dL/dZ_E^0. Forward states are recomputed level by level from the
+    levels' starting rows (checkpoints)."""
+    L = len(h.levels) - 1
+    top = h.levels[L]
+    z = np.asarray(z_coarsest, dtype=np.float64)
+    starts = [None] * (L + 1)
+    starts[L] = (z[:top.n], z[top.n:])
+    zv, ze = refine(top, starts[L][0], starts[L][1], omega, sweeps)
+    for ell in range(L - 1, -1, -1):
+        zv, ze = project(h.rep_v[ell], h.rep_e[ell], zv, ze)
+        starts[ell] = (zv, ze)
+        zv, ze = refine(h.levels[ell], zv, ze, omega, sweeps)
+    m0 = h.levels[0].m
+    dw0 = np.zeros(m0)
+    g_v, g_e = np.asarray(g_v0, dtype=np.float64), np.asarray(g_e0, dtype=np.float64)
+    for ell in range(0, L + 1):
+        lv = h.levels[ell]
+        states = refine_states(lv, starts[ell][0], starts[ell][1], omega, sweeps)
+        g_v, g_e, dw = refine_backward(lv, states, omega, g_v, g_e)
+        np.add.at(dw0, lv.orig_e, dw)
+        if ell < L:
+            nxt = h.levels[ell + 1]
+            g_v, g_e = project_backward(h.rep_v[ell], h.rep_e[ell], nxt.n, nxt.m, g_v, g_e)
+    return dw0, np.vstack([g_v, g_e])
