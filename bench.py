@@ -437,21 +437,8 @@ def run_refine_level(args):
 
 
 # ---------------------------------------------------------------------------
-# Precision study: BF16 storage vs FP32 on the same GPU, and both vs the
-# FP64 oracle on an induced subsample
+# Precision study: BF16 storage vs FP32 on the same GPU
 # ---------------------------------------------------------------------------
-
-def _oracle_vcycle_cols(args):
-    """Oracle V-cycle on a block of embedding columns (refinement acts on each
-    column independently, so column blocks can run in separate processes)."""
-    hg_arrays, params, zc_block, sweeps = args
-    from oracle import hnv_oracle as O
-    n, m, ptr, nodes, w = hg_arrays
-    lv0 = O.build_level(n, m, ptr, nodes, w)
-    h = O.coarsen(lv0, O.CoarsenParams(**params))
-    res = O.vcycle(h, zc_block, 0.5, sweeps, keep_levels=True)
-    return [np.vstack(p) for p in res.per_level]
-
 
 def gpu_levels(H, G, zc, sweeps):
     """The V-cycle run level by level through the ABI; returns each level's
@@ -489,57 +476,30 @@ def level_errors(got, ref):
 
 
 def run_precision_study(args):
-    import multiprocessing as mp
+    """BF16 storage vs FP32 on the same GPU: V-cycle time and per-level
+    difference, both precisions starting from the same bfloat16-rounded
+    coarsest rows. (The comparison with the FP64 oracle on an induced
+    subsample is a GPU test: tests/test_gpu_fullsize.py.)"""
     import torch
-    spec = hypergen.CONFIGS[args.workload]
-    hg = hypergen.generate(spec)
-    sub = hypergen.induced_subhypergraph(hg, min(args.subsample, hg.n), seed=spec.seed)
-    params = dict(min_nodes=spec.min_nodes, max_levels=spec.max_levels, seed=spec.seed)
-    # the seeded coarsest rows of the subsample, rounded to bfloat16 once:
-    # both GPU precisions and the oracle start from exactly these values
     import paper_2103_09660_gb300 as H
     from paper_2103_09660_gb300 import build as B
     B.build()
+    spec = hypergen.CONFIGS[args.workload]
+    hg = hypergen.generate(spec)
+    params = dict(min_nodes=spec.min_nodes, max_levels=spec.max_levels, seed=spec.seed)
     dev = torch.device("cuda", 0)
-    with H.Graph.from_hypergraph(sub, on_device=True) as G:
-        L = G.coarsen(**params)
-        nL, mL, _ = G.level_info(L - 1)
-    zc = torch.from_numpy(hypergen.coarsest_embedding(nL + mL, spec.d, seed=spec.seed))
-    zc = zc.to(torch.bfloat16).float()
-    # oracle: column blocks in spawned workers
-    blocks = max(1, min(16, (os.cpu_count() or 1)))
-    cols = np.array_split(np.arange(spec.d), blocks)
-    arrays = (sub.n, sub.m, sub.edge_ptr, sub.edge_nodes, sub.weights)
-    t0 = time.perf_counter()
-    with mp.get_context("spawn").Pool(blocks) as pool:
-        parts = pool.map(_oracle_vcycle_cols,
-                         [(arrays, params, zc.numpy()[:, c].astype(np.float64), spec.sweeps)
-                          for c in cols])
-    oracle_s = time.perf_counter() - t0
-    ref = [np.hstack([p[l] for p in parts]) for l in range(len(parts[0]))]
-    sub_rows = []
-    with H.Graph.from_hypergraph(sub, on_device=True) as G:
-        G.coarsen(**params)
-        z32 = gpu_levels(H, G, zc.to(dev), spec.sweeps)
-        z16 = gpu_levels(H, G, zc.to(dev).to(torch.bfloat16), spec.sweeps)
-        for l in range(len(ref)):
-            r = torch.from_numpy(ref[l]).to(dev)
-            sub_rows.append({"level": l, "fp32_vs_fp64": level_errors(z32[l], r),
-                             "bf16_vs_fp64": level_errors(z16[l], r)})
-    del z32, z16
-    # full size: timing and BF16 vs FP32 per level
-    full_rows = []
+    rows = []
     timing = {}
     with H.Graph.from_hypergraph(hg, on_device=True) as G:
         L = G.coarsen(**params)
         sizes = [G.level_info(l) for l in range(L)]
         nL, mL, _ = sizes[-1]
-        zc_full = torch.from_numpy(hypergen.coarsest_embedding(nL + mL, spec.d, seed=spec.seed))
-        zc_full = zc_full.to(torch.bfloat16).to(dev)
+        zc = torch.from_numpy(hypergen.coarsest_embedding(nL + mL, spec.d, seed=spec.seed))
+        zc = zc.to(torch.bfloat16).to(dev)
         for name, dt in (("fp32", torch.float32), ("bf16", torch.bfloat16)):
             zv = torch.empty((hg.n, spec.d), dtype=dt, device=dev)
             ze = torch.empty((hg.m, spec.d), dtype=dt, device=dev)
-            zci = zc_full.to(dt)
+            zci = zc.to(dt)
             G.vcycle(zci, zv, ze, 0.5, spec.sweeps)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -551,11 +511,11 @@ def run_precision_study(args):
             G.sync_status()
             timing[name] = e0.elapsed_time(e1) / args.steps
             del zv, ze
-        z32 = gpu_levels(H, G, zc_full.float(), spec.sweeps)
-        z16 = gpu_levels(H, G, zc_full, spec.sweeps)
+        z32 = gpu_levels(H, G, zc.float(), spec.sweeps)
+        z16 = gpu_levels(H, G, zc, spec.sweeps)
         for l in range(L):
-            full_rows.append({"level": l, "n": sizes[l][0], "m": sizes[l][1], "nnz": sizes[l][2],
-                              "bf16_vs_fp32": level_errors(z16[l], z32[l])})
+            rows.append({"level": l, "n": sizes[l][0], "m": sizes[l][1], "nnz": sizes[l][2],
+                         "bf16_vs_fp32": level_errors(z16[l], z32[l])})
     updates = float(sum(2.0 * nnz * spec.d * spec.sweeps for (_, _, nnz) in sizes))
     print(json.dumps({
         "study": "bf16 storage vs fp32", "workload": args.workload,
@@ -563,10 +523,72 @@ def run_precision_study(args):
         "vcycle_ms": timing, "speedup_bf16_over_fp32": timing["fp32"] / timing["bf16"],
         "refine_updates_per_s": {k: updates / (v / 1e3) for k, v in timing.items()},
         "error_metrics": "(max|diff|/max|ref|, max row-relative with 1e-3 rms floor)",
-        "full_size_levels": full_rows,
-        "subsample": {"nodes": sub.n, "hyperedges": sub.m, "nnz": sub.nnz,
-                      "oracle_seconds": round(oracle_s, 1), "oracle_processes": blocks,
-                      "levels": sub_rows}}))
+        "levels": rows}))
+
+
+# ---------------------------------------------------------------------------
+# Differentiation study: forward + backward of a node-classification loss
+# through the V-cycle, against the forward alone
+# ---------------------------------------------------------------------------
+
+def run_autograd_study(args):
+    """Forward + backward of a node-classification loss through the V-cycle
+    against the forward alone (float32). (Gradient parity with the FP64
+    oracle at this size is a GPU test: tests/test_gpu_fullsize.py.)"""
+    import torch
+    import paper_2103_09660_gb300 as H
+    from paper_2103_09660_gb300 import build as B
+    B.build()
+    spec = hypergen.CONFIGS[args.workload]
+    hg = hypergen.generate(spec)
+    params = dict(min_nodes=spec.min_nodes, max_levels=spec.max_levels, seed=spec.seed)
+    om, k, d = 0.5, spec.sweeps, spec.d
+    classes = int(hg.labels.max()) + 1
+    gen = torch.Generator().manual_seed(spec.seed)
+    head = torch.randn(d, classes, generator=gen) / d ** 0.5
+    sub = torch.randperm(hg.n, generator=gen)[: hg.n // 10]
+    labels = torch.from_numpy(hg.labels.astype(np.int64))[sub]
+    dev = torch.device("cuda", 0)
+    with H.Graph.from_hypergraph(hg, on_device=True) as G:
+        L = G.coarsen(**params)
+        nL, mL, _ = G.level_info(L - 1)
+        zc = torch.from_numpy(hypergen.coarsest_embedding(nL + mL, d, seed=spec.seed)).to(dev)
+        w0 = torch.from_numpy(hg.weights.copy()).to(dev)
+        head_d, sub_d, lab_d = head.to(dev), sub.to(dev), labels.to(dev)
+        zv = torch.empty((hg.n, d), device=dev)
+        ze = torch.empty((hg.m, d), device=dev)
+        G.set_weights(w0)
+
+        def fwd():
+            H.hnv_vcycle(G.handle, zc, zv, ze, om, k, H.SWEEP_TWO_PHASE, G.stream)
+
+        def fwd_bwd():
+            w = w0.clone().requires_grad_(True)
+            z = zc.clone().requires_grad_(True)
+            zvo, _ = H.vcycle_autograd(G, w, z, om, k)
+            torch.nn.functional.cross_entropy(zvo[sub_d] @ head_d, lab_d).backward()
+
+        def timed(fn, reps):
+            for _ in range(2):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        t_fwd = timed(fwd, args.steps)
+        t_fb = timed(fwd_bwd, args.steps)
+        G.sync_status()
+    print(json.dumps({
+        "study": "forward+backward vs forward (float32)", "workload": args.workload,
+        "n": hg.n, "m": hg.m, "nnz": hg.nnz, "d": d, "levels": L, "sweeps_per_level": k,
+        "loss": "softmax cross-entropy of a seeded %dx%d linear head on a seeded %d-node subset"
+                % (d, classes, len(sub)),
+        "forward_ms": t_fwd, "forward_backward_ms": t_fb, "ratio": t_fb / t_fwd}))
 
 
 def main(argv=None):
@@ -583,9 +605,9 @@ def main(argv=None):
     ap.add_argument("--dtype", choices=["f32", "bf16"], default="f32",
                     help="embedding storage of the timed V-cycle (sums are float32 either way)")
     ap.add_argument("--precision-study", action="store_true",
-                    help="BF16 vs FP32 per level at full size, both vs the FP64 oracle on an "
-                         "induced subsample (use with --workload planted_4m)")
-    ap.add_argument("--subsample", type=int, default=250_000)
+                    help="BF16 vs FP32 per level and V-cycle time (use with --workload planted_4m)")
+    ap.add_argument("--autograd-study", action="store_true",
+                    help="forward+backward vs forward time (use with --workload diff_200k)")
     args = ap.parse_args(argv)
     ws, rank, local = dist_env()
     if args.refine_level is not None:
@@ -593,6 +615,9 @@ def main(argv=None):
         return
     if args.precision_study:
         run_precision_study(args)
+        return
+    if args.autograd_study:
+        run_autograd_study(args)
         return
     if args.impl == "reference":
         line = run_reference(args, ws, rank, local)

@@ -228,6 +228,46 @@ int hnv_vcycle(hnv_graph* g, const void* z_coarsest, void* z_v_out, void* z_e_ou
 int hnv_refine_noalloc(hnv_graph* g, int level, void* z_v, void* z_e, hnv_dtype dt, int d,
                        float omega, int sweeps, hnv_stream_t stream);
 
+/* ---------------------------------------------------------------------------
+ * Differentiation (reverse mode of the two-phase float32 V-cycle)
+ *
+ * The V-cycle maps (w0, Z^L) -> (Z_V^0, Z_E^0), where w0 are the level-0
+ * hyperedge weights (a coarse hyperedge keeps the weight of the level-0
+ * hyperedge it represents) and Z^L the coarsest rows. The weights enter the
+ * node half-sweeps of Algorithm 2 through the weighted neighbour mean of
+ * Section 3.3. The hierarchy itself does not depend on the weights under
+ * HNV_ASSIGN_HASH / LOW_DEGREE / EXPLICIT (it does under HIGH_WEIGHT).
+ * ------------------------------------------------------------------------- */
+
+/* Replaces the level-0 weights (float32 [m0], finite and > 0; host or device)
+ * and every level's weight-dependent arrays. Synchronises the stream. */
+int hnv_set_weights(hnv_graph* g, const float* w0, int on_device, hnv_stream_t stream);
+
+/* Size (in floats) of the checkpoint buffer hnv_vcycle_save writes for width
+ * d: sum over levels of (n_l + m_l) * d. */
+int hnv_checkpoint_floats(const hnv_graph* g, int d, int64_t* floats);
+
+/* hnv_vcycle (two-phase, float32, device buffers) that also saves every
+ * level's starting rows (after projection; the coarsest level's input) into
+ * `checkpoints` (device, hnv_checkpoint_floats floats) for the backward pass. */
+int hnv_vcycle_save(hnv_graph* g, const float* z_coarsest, float* z_v_out, float* z_e_out, int d,
+                    float omega, int sweeps_per_level, float* checkpoints, hnv_stream_t stream);
+
+/* Reverse mode of hnv_vcycle_save. Given dL/dZ_V^0 (g_v0 [n0 x d]) and
+ * dL/dZ_E^0 (g_e0 [m0 x d]; either may be NULL = zero), writes dL/dw0
+ * (grad_w0 [m0]) and dL/dZ^L (grad_z_coarsest [(n_L + m_L) x d]). Every
+ * level's sweeps are recomputed from its checkpoint, then reversed:
+ *   node half:      a_v = G_V/D_v, A_e = sum_{v in e} a_v,
+ *                   dw_e += omega (<A_e, z_e> - sum_{v in e} <a_v, z~_v>),
+ *                   G_E += omega w_e A_e, G_V *= 1 - omega;
+ *   hyperedge half: G_V += omega sum_{e ∋ v} G_E[e]/|e|, G_E *= 1 - omega;
+ * projection reverses to a segmented sum over each coarse row's copies. The
+ * weights, omega, d and sweeps must be those of the forward call. All device
+ * buffers; asynchronous on the stream; deterministic. */
+int hnv_vcycle_backward(hnv_graph* g, const float* checkpoints, const float* g_v0,
+                        const float* g_e0, float* grad_w0, float* grad_z_coarsest, int d,
+                        float omega, int sweeps_per_level, hnv_stream_t stream);
+
 /* Synchronises `stream` and reports device-side failures of the graph's
  * asynchronous calls since the last check: HNV_ERR_TIMEOUT if a bounded
  * device wait of a refinement kernel gave up (its results are then invalid),

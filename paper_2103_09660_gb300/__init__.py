@@ -28,7 +28,8 @@ __all__ = [
     "ARR_REP_E", "ARR_DEG_V",
     "PHASE_BUILD", "PHASE_COARSEN", "PHASE_PROJECT", "PHASE_REFINE_E", "PHASE_REFINE_V",
     "Graph", "hnv_build_incidence", "hnv_coarsen", "hnv_project", "hnv_refine",
-    "hnv_vcycle", "hnv_refine_noalloc", "kernel_launch_count", "timing_enable", "timing_reset", "timing_read",
+    "hnv_vcycle", "hnv_refine_noalloc", "hnv_set_weights", "hnv_checkpoint_floats",
+    "hnv_vcycle_save", "hnv_vcycle_backward", "vcycle_autograd", "kernel_launch_count", "timing_enable", "timing_reset", "timing_read",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -84,6 +85,10 @@ def _declare(L):
         "hnv_refine_noalloc": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_int, f32, ctypes.c_int, _P]),
         "hnv_graph_free": (None, [_P]),
         "hnv_sync_status": (ctypes.c_int, [_P, _P]),
+        "hnv_set_weights": (ctypes.c_int, [_P, _P, ctypes.c_int, _P]),
+        "hnv_checkpoint_floats": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(i64)]),
+        "hnv_vcycle_save": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, f32, ctypes.c_int, _P, _P]),
+        "hnv_vcycle_backward": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.c_int, f32, ctypes.c_int, _P]),
         "hnv_error_string": (ctypes.c_char_p, [ctypes.c_int]),
         "hnv_last_error_detail": (ctypes.c_char_p, []),
         "hnv_set_allocator": (ctypes.c_int, [_P, _P, _P]),
@@ -248,6 +253,104 @@ def hnv_vcycle(g: int, z_coarsest, z_v_out, z_e_out, omega: float = 0.5, sweeps:
                             _stream_handle(stream)), "hnv_vcycle")
 
 
+def hnv_set_weights(g: int, w0, stream=None):
+    """Level-0 hyperedge weights (numpy float32 or a float32 tensor, host or
+    device) for every level of the hierarchy."""
+    import torch
+    if isinstance(w0, torch.Tensor):
+        t = w0.detach().contiguous().float()
+        on_dev = 1 if t.is_cuda else 0
+        _check(lib().hnv_set_weights(g, t.data_ptr(), on_dev, _stream_handle(stream)),
+               "hnv_set_weights")
+    else:
+        a = np.ascontiguousarray(w0, dtype=np.float32)
+        _check(lib().hnv_set_weights(g, a.ctypes.data, 0, _stream_handle(stream)),
+               "hnv_set_weights")
+
+
+def hnv_checkpoint_floats(g: int, d: int) -> int:
+    out = ctypes.c_int64()
+    _check(lib().hnv_checkpoint_floats(g, int(d), ctypes.byref(out)), "hnv_checkpoint_floats")
+    return out.value
+
+
+def hnv_vcycle_save(g: int, z_coarsest, z_v_out, z_e_out, checkpoints, omega: float = 0.5,
+                    sweeps: int = 10, stream=None):
+    import torch
+    d = z_coarsest.shape[1]
+    _check(lib().hnv_vcycle_save(g, _dev_ptr(z_coarsest, torch.float32, "z_coarsest"),
+                                 _dev_ptr(z_v_out, torch.float32, "z_v_out"),
+                                 _dev_ptr(z_e_out, torch.float32, "z_e_out"), int(d),
+                                 float(omega), int(sweeps),
+                                 _dev_ptr(checkpoints, torch.float32, "checkpoints"),
+                                 _stream_handle(stream)), "hnv_vcycle_save")
+
+
+def hnv_vcycle_backward(g: int, checkpoints, g_v0, g_e0, grad_w0, grad_z_coarsest,
+                        omega: float = 0.5, sweeps: int = 10, stream=None):
+    import torch
+    d = grad_z_coarsest.shape[1]
+    gv = _dev_ptr(g_v0, torch.float32, "g_v0") if g_v0 is not None else None
+    ge = _dev_ptr(g_e0, torch.float32, "g_e0") if g_e0 is not None else None
+    _check(lib().hnv_vcycle_backward(g, _dev_ptr(checkpoints, torch.float32, "checkpoints"), gv,
+                                     ge, _dev_ptr(grad_w0, torch.float32, "grad_w0"),
+                                     _dev_ptr(grad_z_coarsest, torch.float32, "grad_z_coarsest"),
+                                     int(d), float(omega), int(sweeps), _stream_handle(stream)),
+           "hnv_vcycle_backward")
+
+
+def _autograd_function():
+    import torch
+
+    class VCycleFunction(torch.autograd.Function):
+        """(w0, Z^L) -> (Z_V^0, Z_E^0) through the two-phase float32 V-cycle;
+        backward runs the library's adjoint (per-level checkpoints, sweeps
+        recomputed)."""
+
+        @staticmethod
+        def forward(ctx, w0, z_coarsest, graph, omega, sweeps):
+            w = w0.detach().contiguous().float()
+            zc = z_coarsest.detach().contiguous().float()
+            graph.set_weights(w)
+            n0, m0, _ = graph.level_info(0)
+            d = zc.shape[1]
+            ckpt = torch.empty(hnv_checkpoint_floats(graph.handle, d), device=zc.device)
+            zv = torch.empty((n0, d), device=zc.device)
+            ze = torch.empty((m0, d), device=zc.device)
+            hnv_vcycle_save(graph.handle, zc, zv, ze, ckpt, omega, sweeps, graph.stream)
+            ctx.graph, ctx.ckpt, ctx.w = graph, ckpt, w
+            ctx.omega, ctx.sweeps, ctx.zc_shape = omega, sweeps, tuple(zc.shape)
+            return zv, ze
+
+        @staticmethod
+        def backward(ctx, g_v, g_e):
+            graph = ctx.graph
+            graph.set_weights(ctx.w)      # the weights of the forward call
+            dev = ctx.ckpt.device
+            m0 = ctx.w.shape[0]
+            gw = torch.empty(m0, device=dev)
+            gz = torch.empty(ctx.zc_shape, device=dev)
+            hnv_vcycle_backward(graph.handle, ctx.ckpt,
+                                g_v.contiguous().float() if g_v is not None else None,
+                                g_e.contiguous().float() if g_e is not None else None,
+                                gw, gz, ctx.omega, ctx.sweeps, graph.stream)
+            return gw, gz, None, None, None
+
+    return VCycleFunction
+
+
+_VCYCLE_FN = None
+
+
+def vcycle_autograd(graph, w0, z_coarsest, omega: float = 0.5, sweeps: int = 10):
+    """Differentiable V-cycle: returns (Z_V^0, Z_E^0); gradients flow to the
+    level-0 hyperedge weights w0 and the coarsest rows z_coarsest."""
+    global _VCYCLE_FN
+    if _VCYCLE_FN is None:
+        _VCYCLE_FN = _autograd_function()
+    return _VCYCLE_FN.apply(w0, z_coarsest, graph, float(omega), int(sweeps))
+
+
 def kernel_launch_count() -> int:
     return int(lib().hnv_kernel_launch_count())
 
@@ -312,6 +415,9 @@ class Graph:
         """Synchronise the graph's stream and raise if a device-side wait of
         an asynchronous call gave up (HNV_ERR_TIMEOUT)."""
         _check(lib().hnv_sync_status(self.handle, _stream_handle(self.stream)), "hnv_sync_status")
+
+    def set_weights(self, w0):
+        hnv_set_weights(self.handle, w0, self.stream)
 
     def coarsen(self, **kw) -> int:
         return hnv_coarsen(self.handle, **kw)

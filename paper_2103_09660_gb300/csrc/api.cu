@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "hnv_internal.cuh"
 
@@ -78,8 +79,11 @@ void drop_maps(Level* lv, cudaStream_t s) {
   lv->rep_e = nullptr;
 }
 
+// ckpt (optional, device, float32 only): every level's starting rows (node
+// rows then hyperedge rows) at float offset sum_{j<l} (n_j + m_j) * d.
 int vcycle_impl(hnv_graph* g, const void* z_coarsest, void* z_v_out, void* z_e_out, int dtype,
-                int d, float omega, int sweeps, int mode, int on_device, cudaStream_t s) {
+                int d, float omega, int sweeps, int mode, int on_device, cudaStream_t s,
+                float* ckpt = nullptr) {
   const int L = (int)g->levels.size() - 1;
   const size_t row_bytes = dtype_size((hnv_dtype)dtype) * (size_t)d;
   TempPool pool(s);
@@ -108,9 +112,25 @@ int vcycle_impl(hnv_graph* g, const void* z_coarsest, void* z_v_out, void* z_e_o
   if (top.n > 0) HNV_CUDA(cudaMemcpyAsync(zv(L), zc, row_bytes * top.n, kind, s));
   if (top.m > 0)
     HNV_CUDA(cudaMemcpyAsync(ze(L), zc + (size_t)top.n * row_bytes, row_bytes * top.m, kind, s));
+  std::vector<size_t> off(L + 2, 0);
+  for (int l = 0; l <= L; ++l)
+    off[l + 1] = off[l] + ((size_t)g->levels[l].n + g->levels[l].m) * row_bytes;
+  auto save = [&](int l) -> int {
+    if (!ckpt) return HNV_OK;
+    uint8_t* c = reinterpret_cast<uint8_t*>(ckpt) + off[l];
+    const Level& lv = g->levels[l];
+    if (lv.n > 0)
+      HNV_CUDA(cudaMemcpyAsync(c, zv(l), row_bytes * lv.n, cudaMemcpyDeviceToDevice, s));
+    if (lv.m > 0)
+      HNV_CUDA(cudaMemcpyAsync(c + row_bytes * lv.n, ze(l), row_bytes * lv.m,
+                               cudaMemcpyDeviceToDevice, s));
+    return HNV_OK;
+  };
+  HNV_CHECK(save(L));
   HNV_CHECK(refine_level(g, L, zv(L), ze(L), dtype, d, omega, sweeps, mode, s));
   for (int l = L - 1; l >= 0; --l) {
     HNV_CHECK(project_level(g, l, zv(l + 1), ze(l + 1), zv(l), ze(l), dtype, d, s));
+    HNV_CHECK(save(l));
     HNV_CHECK(refine_level(g, l, zv(l), ze(l), dtype, d, omega, sweeps, mode, s));
   }
   if (!on_device) {
@@ -398,6 +418,70 @@ int hnv_vcycle(hnv_graph* g, const void* z_coarsest, void* z_v_out, void* z_e_ou
   DeviceGuard dgd(g->device);
   return vcycle_impl(g, z_coarsest, z_v_out, z_e_out, (int)dt, d, omega, sweeps_per_level,
                      (int)mode, buffers_on_device, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int hnv_set_weights(hnv_graph* g, const float* w0, int on_device, hnv_stream_t stream) {
+  clear_error_detail();
+  if (!g) HNV_FAIL(HNV_ERR_INVALID_ARG, "graph is NULL");
+  const int32_t m0 = g->levels[0].m;
+  if (m0 > 0 && !w0) HNV_FAIL(HNV_ERR_INVALID_ARG, "w0 is NULL");
+  DeviceGuard dgd(g->device);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  TempPool pool(s);
+  const float* d_w0 = w0;
+  if (!on_device && m0 > 0) {
+    float* t = nullptr;
+    HNV_CHECK(pool.get(&t, (size_t)m0));
+    HNV_CUDA(cudaMemcpyAsync(t, w0, sizeof(float) * m0, cudaMemcpyHostToDevice, s));
+    d_w0 = t;
+  }
+  return set_weights_impl(g, d_w0, s);
+}
+
+int hnv_checkpoint_floats(const hnv_graph* g, int d, int64_t* floats) {
+  if (!g || !floats) HNV_FAIL(HNV_ERR_INVALID_ARG, "NULL argument");
+  int64_t t = 0;
+  for (const Level& lv : g->levels) t += ((int64_t)lv.n + lv.m) * d;
+  *floats = t;
+  return HNV_OK;
+}
+
+int hnv_vcycle_save(hnv_graph* g, const float* z_coarsest, float* z_v_out, float* z_e_out, int d,
+                    float omega, int sweeps_per_level, float* checkpoints, hnv_stream_t stream) {
+  clear_error_detail();
+  if (!g) HNV_FAIL(HNV_ERR_INVALID_ARG, "graph is NULL");
+  HNV_CHECK(check_embedding_args(HNV_F32, d));
+  if (!(omega >= 0.f && omega <= 1.f)) HNV_FAIL(HNV_ERR_INVALID_ARG, "omega must be in [0, 1]");
+  if (sweeps_per_level < 0) HNV_FAIL(HNV_ERR_INVALID_ARG, "sweeps_per_level < 0");
+  const Level& top = g->levels.back();
+  const Level& l0 = g->levels[0];
+  HNV_CHECK(check_buf(z_coarsest, (int64_t)top.n + top.m, "z_coarsest"));
+  HNV_CHECK(check_buf(z_v_out, l0.n, "z_v_out"));
+  HNV_CHECK(check_buf(z_e_out, l0.m, "z_e_out"));
+  HNV_CHECK(check_buf(checkpoints, 1, "checkpoints"));
+  DeviceGuard dgd(g->device);
+  return vcycle_impl(g, z_coarsest, z_v_out, z_e_out, HNV_F32, d, omega, sweeps_per_level,
+                     HNV_SWEEP_TWO_PHASE, 1, reinterpret_cast<cudaStream_t>(stream), checkpoints);
+}
+
+int hnv_vcycle_backward(hnv_graph* g, const float* checkpoints, const float* g_v0,
+                        const float* g_e0, float* grad_w0, float* grad_z_coarsest, int d,
+                        float omega, int sweeps_per_level, hnv_stream_t stream) {
+  clear_error_detail();
+  if (!g) HNV_FAIL(HNV_ERR_INVALID_ARG, "graph is NULL");
+  HNV_CHECK(check_embedding_args(HNV_F32, d));
+  if (!(omega >= 0.f && omega <= 1.f)) HNV_FAIL(HNV_ERR_INVALID_ARG, "omega must be in [0, 1]");
+  if (sweeps_per_level < 0) HNV_FAIL(HNV_ERR_INVALID_ARG, "sweeps_per_level < 0");
+  const Level& top = g->levels.back();
+  const Level& l0 = g->levels[0];
+  HNV_CHECK(check_buf(checkpoints, 1, "checkpoints"));
+  HNV_CHECK(check_buf(g_v0, 0, "g_v0"));
+  HNV_CHECK(check_buf(g_e0, 0, "g_e0"));
+  HNV_CHECK(check_buf(grad_w0, l0.m, "grad_w0"));
+  HNV_CHECK(check_buf(grad_z_coarsest, (int64_t)top.n + top.m, "grad_z_coarsest"));
+  DeviceGuard dgd(g->device);
+  return vcycle_backward_impl(g, checkpoints, g_v0, g_e0, grad_w0, grad_z_coarsest, d, omega,
+                              sweeps_per_level, reinterpret_cast<cudaStream_t>(stream));
 }
 
 int hnv_sync_status(hnv_graph* g, hnv_stream_t stream) {

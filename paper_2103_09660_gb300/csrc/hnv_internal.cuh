@@ -195,6 +195,13 @@ struct Level {
   int32_t* rep_v = nullptr;      // [n] -> level+1 (null on the coarsest)
   int32_t* rep_e = nullptr;      // [m] -> level+1 or -1-c
   SplitPlan planE, planV;
+  // adjoint (built on first use; freed with the level)
+  bool adj_ready = false;
+  float* e_invdeg_w = nullptr;   // [nnz] CSR order: 1/deg_v of each member
+  float* v_invsize_w = nullptr;  // [nnz] CSC order: 1/|e| of each hyperedge
+  int32_t* ch_ptr = nullptr;     // [n_{l+1}+1] children of each coarse node:
+  int32_t* ch_idx = nullptr;     //   fine nodes v, then collapsed hyperedges n + e
+  SplitPlan planC;
   std::vector<void*> owned;      // every device allocation of this level
 };
 
@@ -219,6 +226,11 @@ namespace hnv {
 int build_level0(hnv_graph* g, int32_t n, int32_t m, const int64_t* d_edge_ptr,
                  const int32_t* d_edge_nodes, const float* d_w, Level* out);
 int finish_level(hnv_graph* g, Level* lv);   // derived arrays + plans
+// Weight-dependent arrays of a level (v_w, deg_v, inv_deg_v) from lv->w.
+int level_weight_arrays(Level* lv, cudaStream_t s);
+// Split-row work plan of a CSR with `rows` rows (allocations owned by lv).
+int build_split_plan(hnv_graph* g, Level* lv, const int32_t* ptr, int32_t rows, SplitPlan* plan,
+                     cudaStream_t s);
 void free_level(Level* lv, cudaStream_t s);
 int level_alloc(Level* lv, void** p, size_t bytes, cudaStream_t s);
 
@@ -232,12 +244,26 @@ int refine_level(hnv_graph* g, int level, void* z_v, void* z_e, int dtype, int d
                  int sweeps, int mode, cudaStream_t s);
 int project_level(const hnv_graph* g, int fine_level, const void* zc_v, const void* zc_e,
                   void* zf_v, void* zf_e, int dtype, int d, cudaStream_t s);
+// adjoint.cu: weights from a level-0 weight vector (device) to every level,
+// and the reverse mode of the two-phase float32 V-cycle.
+int set_weights_impl(hnv_graph* g, const float* d_w0, cudaStream_t s);
+int vcycle_backward_impl(hnv_graph* g, const float* ckpt, const float* g_v0, const float* g_e0,
+                         float* grad_w0, float* grad_zc, int d, float omega, int sweeps,
+                         cudaStream_t s);
+
 // tma_refine.cu: TMA-gather half-sweep for d in {32, 64, 128, 256}.
 bool tma_supported(int d);
 int tma_half_sweep(const SplitPlan& plan, const int32_t* idx, const float* inc_w,
                    const float* inv_norm, const float* src, int64_t src_rows, const float* self_in,
                    float* out, int64_t self_rows, int d, float omega, float* partials,
                    int32_t* err, cudaStream_t s);
+
+// General float32 row gather over a plan (used by the adjoint):
+// out[r] = keep * self[r] + scale * norm[r] * sum_k wgt[k] * src[idx[k]];
+// norm / wgt may be null (1); with keep == 0 self is not read.
+int gather_rows_f32(const SplitPlan& plan, const int32_t* idx, const float* wgt,
+                    const float* norm, const float* src, const float* self_in, float* out, int d,
+                    float keep, float scale, float* partials, cudaStream_t s);
 
 // Two-phase sweeps whose split-row partial sums go to caller-provided
 // scratch (at least max(planE.n_chunks, planV.n_chunks) * d floats); no

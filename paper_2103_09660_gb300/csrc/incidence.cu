@@ -215,8 +215,8 @@ int read_and_clear_err(hnv_graph* g, cudaStream_t s, int32_t* bits) {
   return HNV_OK;
 }
 
-static int build_plan(hnv_graph* g, Level* lv, const int32_t* ptr, int32_t rows, SplitPlan* plan,
-                      cudaStream_t s) {
+int build_split_plan(hnv_graph* g, Level* lv, const int32_t* ptr, int32_t rows, SplitPlan* plan,
+                     cudaStream_t s) {
   *plan = SplitPlan();
   const int32_t T = plan->T;
   if (rows == 0) return HNV_OK;
@@ -271,6 +271,13 @@ static int build_plan(hnv_graph* g, Level* lv, const int32_t* ptr, int32_t rows,
   return HNV_OK;
 }
 
+int level_weight_arrays(Level* lv, cudaStream_t s) {
+  HNV_CHECK(launch("csc_weights", csc_weights_kernel, grid_for(lv->nnz, 256), 256, 0, s, lv->nnz,
+                   (const int32_t*)lv->v_edges, (const float*)lv->w, lv->v_w));
+  return launch("deg", deg_kernel, grid_for((int64_t)lv->n * 32, 256), 256, 0, s, lv->n,
+                (const int32_t*)lv->v_ptr, (const float*)lv->v_w, lv->deg_v, lv->inv_deg_v);
+}
+
 int finish_level(hnv_graph* g, Level* lv) {
   cudaStream_t s = g->stream;
   const int32_t n = lv->n, m = lv->m;
@@ -284,12 +291,9 @@ int finish_level(hnv_graph* g, Level* lv) {
   HNV_CHECK(level_alloc(lv, (void**)&lv->inv_deg_v, sizeof(float) * (size_t)n, s));
   HNV_CHECK(launch("inv_size", inv_size_kernel, grid_for(m, 256), 256, 0, s, m,
                    (const int32_t*)lv->e_ptr, lv->inv_size_e));
-  HNV_CHECK(launch("csc_weights", csc_weights_kernel, grid_for(nnz, 256), 256, 0, s, nnz,
-                   (const int32_t*)lv->v_edges, (const float*)lv->w, lv->v_w));
-  HNV_CHECK(launch("deg", deg_kernel, grid_for((int64_t)n * 32, 256), 256, 0, s, n,
-                   (const int32_t*)lv->v_ptr, (const float*)lv->v_w, lv->deg_v, lv->inv_deg_v));
-  HNV_CHECK(build_plan(g, lv, lv->e_ptr, m, &lv->planE, s));
-  HNV_CHECK(build_plan(g, lv, lv->v_ptr, n, &lv->planV, s));
+  HNV_CHECK(level_weight_arrays(lv, s));
+  HNV_CHECK(build_split_plan(g, lv, lv->e_ptr, m, &lv->planE, s));
+  HNV_CHECK(build_split_plan(g, lv, lv->v_ptr, n, &lv->planV, s));
   return HNV_OK;
 }
 

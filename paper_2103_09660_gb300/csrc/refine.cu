@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(256)
 gather_kernel(const int4* __restrict__ items, int32_t n_items, const int32_t* __restrict__ idx,
               const float* __restrict__ inc_w, const float* __restrict__ inv_norm,
               const uint4* __restrict__ src, const uint4* self_in, uint4* out, int32_t dv,
-              float omega, float* __restrict__ partials) {
+              float keep, float scale, float* __restrict__ partials) {
   using V = VecT<T>;
   constexpr int N = V::N;
   constexpr int R = 32 / G;                                    // items per warp pass
@@ -93,7 +93,7 @@ gather_kernel(const int4* __restrict__ items, int32_t n_items, const int32_t* __
   const int grp = lane / G;
   const int lg = lane & (G - 1);
   const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
-  const float keep = 1.0f - omega;
+  const bool read_self = keep != 0.f;
   const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
 
   for (int64_t wbase = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * R;
@@ -105,11 +105,13 @@ gather_kernel(const int4* __restrict__ items, int32_t n_items, const int32_t* __
     const bool is_row = (row >= 0) && (slot < 0);
 
     uint4 sv[VPL];
-    if (is_row) {
+#pragma unroll
+    for (int j = 0; j < VPL; ++j) sv[j] = zero4;
+    if (is_row && read_self) {
 #pragma unroll
       for (int j = 0; j < VPL; ++j) {
         const int col = lg + j * G;
-        sv[j] = (col < dv) ? self_in[(size_t)row * dv + col] : zero4;
+        if (col < dv) sv[j] = self_in[(size_t)row * dv + col];
       }
     }
     float acc[VPL][N];
@@ -162,7 +164,7 @@ gather_kernel(const int4* __restrict__ items, int32_t n_items, const int32_t* __
     }
 
     if (is_row) {
-      const float sc = omega * inv_norm[row];
+      const float sc = inv_norm ? scale * inv_norm[row] : scale;
 #pragma unroll
       for (int j = 0; j < VPL; ++j) {
         const int col = lg + j * G;
@@ -190,7 +192,8 @@ gather_kernel(const int4* __restrict__ items, int32_t n_items, const int32_t* __
   }
 }
 
-// Reduces the chunk partials of split rows in chunk order and relaxes.
+// Reduces the chunk partials of split rows in chunk order and relaxes
+// (out = keep * own row + scale * normaliser * sum, as gather_kernel).
 // Blocks [0, mid_blocks) give one warp to each of the first n_mid rows (at
 // most kMidChunks chunks: lanes over row vectors, four interleaved
 // accumulators); each later block takes one of the n_huge rows: S =
@@ -247,23 +250,23 @@ __global__ void __launch_bounds__(kFinThreads)
 finalize_kernel(const int4* __restrict__ long_desc, int32_t n_mid, int32_t n_huge,
                 int32_t mid_blocks, const float* __restrict__ partials,
                 const float* __restrict__ inv_norm, const uint4* self_in, uint4* out,
-                int32_t dv, float omega) {
+                int32_t dv, float keep, float scale) {
   using V = VecT<T>;
   constexpr int N = V::N;
   extern __shared__ float4 sm4[];
   float* sm = reinterpret_cast<float*>(sm4);
-  const float keep = 1.0f - omega;
+  const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
   if ((int32_t)blockIdx.x < mid_blocks) {
     const int32_t k = blockIdx.x * (kFinThreads / 32) + (threadIdx.x >> 5);
     if (k >= n_mid) return;
     const int4 ds = long_desc[k];
     const int lane = threadIdx.x & 31;
-    const float sc = omega * inv_norm[ds.x];
+    const float sc = inv_norm ? scale * inv_norm[ds.x] : scale;
     for (int col = lane; col < dv; col += 32) {
       float tot[N], sf[N], r[N];
       sum_chunks<N>(partials, ds.y, ds.z, dv, col, tot);
       const size_t o = (size_t)ds.x * dv + col;
-      V::unpack(self_in[o], sf);
+      V::unpack(keep != 0.f ? self_in[o] : zero4, sf);
 #pragma unroll
       for (int e = 0; e < N; ++e) r[e] = fmaf(keep, sf[e], sc * tot[e]);
       out[o] = V::pack(r);
@@ -294,8 +297,8 @@ finalize_kernel(const int4* __restrict__ long_desc, int32_t n_mid, int32_t n_hug
 #pragma unroll
       for (int e = 0; e < N; ++e) tot[e] += sm[((size_t)q * dv + col) * N + e];
     const size_t o = (size_t)ds.x * dv + col;
-    V::unpack(self_in[o], sf);
-    const float sc = omega * inv_norm[ds.x];
+    V::unpack(keep != 0.f ? self_in[o] : zero4, sf);
+    const float sc = inv_norm ? scale * inv_norm[ds.x] : scale;
 #pragma unroll
     for (int e = 0; e < N; ++e) r[e] = fmaf(keep, sf[e], sc * tot[e]);
     out[o] = V::pack(r);
@@ -349,6 +352,7 @@ struct HalfSweep {
   int64_t src_rows;        // rows of the neighbour table
   int64_t self_rows;       // rows of this side's table
   int32_t* err;            // device error word (bounded waits)
+  bool allow_tma = true;   // forward relaxations only
 };
 
 // Which gather path the half-sweeps use. The default is the per-lane load
@@ -368,8 +372,8 @@ bool use_tma(int d) {
 
 template <typename T, int G, int VPL>
 int launch_items(const HalfSweep& h, const int4* items, int32_t n_items, const void* src,
-                 const void* self_in, void* out, int dv, float omega, float* partials,
-                 cudaStream_t s) {
+                 const void* self_in, void* out, int dv, float keep, float scale,
+                 float* partials, cudaStream_t s) {
   if (n_items <= 0) return HNV_OK;
   constexpr int R = 32 / G;
   const int64_t warps = ((int64_t)n_items + R - 1) / R;
@@ -378,19 +382,20 @@ int launch_items(const HalfSweep& h, const int4* items, int32_t n_items, const v
   if (h.inc_w)
     return launch("gather_w", gather_kernel<T, G, VPL, true>, blocks, 256, 0, s, items, n_items,
                   h.idx, h.inc_w, h.inv_norm, (const uint4*)src, (const uint4*)self_in,
-                  (uint4*)out, dv, omega, partials);
+                  (uint4*)out, dv, keep, scale, partials);
   return launch("gather", gather_kernel<T, G, VPL, false>, blocks, 256, 0, s, items, n_items,
                 h.idx, h.inc_w, h.inv_norm, (const uint4*)src, (const uint4*)self_in, (uint4*)out,
-                dv, omega, partials);
+                dv, keep, scale, partials);
 }
 
 template <typename T>
 int launch_items_dispatch(int G, int VPL, const HalfSweep& h, const int4* items, int32_t n_items,
-                          const void* src, const void* self_in, void* out, int dv, float omega,
-                          float* partials, cudaStream_t s) {
-#define HNV_CASE(g, v)                                                                     \
-  if (G == g && VPL == v)                                                                  \
-    return launch_items<T, g, v>(h, items, n_items, src, self_in, out, dv, omega, partials, s);
+                          const void* src, const void* self_in, void* out, int dv, float keep,
+                          float scale, float* partials, cudaStream_t s) {
+#define HNV_CASE(g, v)                                                                       \
+  if (G == g && VPL == v)                                                                    \
+    return launch_items<T, g, v>(h, items, n_items, src, self_in, out, dv, keep, scale,     \
+                                 partials, s);
   HNV_CASE(1, 1) HNV_CASE(2, 1) HNV_CASE(4, 1)
   HNV_CASE(8, 1) HNV_CASE(8, 2) HNV_CASE(8, 4) HNV_CASE(8, 8)
   HNV_CASE(16, 1) HNV_CASE(16, 2) HNV_CASE(16, 4) HNV_CASE(16, 8)
@@ -417,14 +422,14 @@ int group_lanes(int cls, int dv) {
 
 template <typename T>
 int run_half(const HalfSweep& h, const void* src, const void* self_in, void* out, int d,
-             float omega, float* partials, cudaStream_t s) {
+             float keep, float scale, float* partials, cudaStream_t s) {
   constexpr int N = VecT<T>::N;
   const int dv = d / N;
   if (dv < 1 || dv > 256) HNV_FAIL(HNV_ERR_UNSUPPORTED_D, "d = %d out of range", d);
   const SplitPlan& p = *h.plan;
-  if (sizeof(T) == 4 && use_tma(d)) {
+  if (sizeof(T) == 4 && h.allow_tma && keep == 1.0f - scale && h.inv_norm && use_tma(d)) {
     HNV_CHECK(tma_half_sweep(p, h.idx, h.inc_w, h.inv_norm, (const float*)src, h.src_rows,
-                             (const float*)self_in, (float*)out, h.self_rows, d, omega, partials,
+                             (const float*)self_in, (float*)out, h.self_rows, d, scale, partials,
                              h.err, s));
   } else {
     const int4* items = p.items;
@@ -435,7 +440,7 @@ int run_half(const HalfSweep& h, const void* src, const void* self_in, void* out
       const int G = group_lanes(cls_lanes[c], dv);
       const int VPL = next_pow2((dv + G - 1) / G);
       HNV_CHECK(launch_items_dispatch<T>(G, VPL, h, items + off, counts[c], src, self_in, out, dv,
-                                         omega, partials, s));
+                                         keep, scale, partials, s));
       off += counts[c];
     }
   }
@@ -446,7 +451,7 @@ int run_half(const HalfSweep& h, const void* src, const void* self_in, void* out
     HNV_CHECK(launch("finalize", finalize_kernel<T>, (unsigned)(mid_blocks + p.n_huge),
                      kFinThreads, smem, s, (const int4*)p.long_desc, p.n_mid, p.n_huge,
                      mid_blocks, (const float*)partials, h.inv_norm, (const uint4*)self_in,
-                     (uint4*)out, dv, omega));
+                     (uint4*)out, dv, keep, scale));
   }
   if (self_in != out && p.n_zero > 0)
     HNV_CHECK(launch("copy_rows", copy_rows_kernel, grid_for((int64_t)p.n_zero * dv, 256), 256, 0,
@@ -457,12 +462,27 @@ int run_half(const HalfSweep& h, const void* src, const void* self_in, void* out
 
 int run_half_dispatch(const HalfSweep& h, const void* src, const void* self_in, void* out,
                       int dtype, int d, float omega, float* partials, cudaStream_t s) {
+  const float keep = 1.0f - omega;
   if (dtype == HNV_BF16)
-    return run_half<__nv_bfloat16>(h, src, self_in, out, d, omega, partials, s);
-  return run_half<float>(h, src, self_in, out, d, omega, partials, s);
+    return run_half<__nv_bfloat16>(h, src, self_in, out, d, keep, omega, partials, s);
+  return run_half<float>(h, src, self_in, out, d, keep, omega, partials, s);
 }
 
 size_t elem_size(int dtype) { return dtype == HNV_BF16 ? 2 : 4; }
+
+}  // namespace
+
+// out[row] = keep * self[row] + scale * norm[row] * sum over the plan's row of
+// wgt[k] * src[idx[k]] (float32 rows; see gather_kernel). norm and wgt may be
+// null (1). The load path only.
+int gather_rows_f32(const SplitPlan& plan, const int32_t* idx, const float* wgt,
+                    const float* norm, const float* src, const float* self_in, float* out, int d,
+                    float keep, float scale, float* partials, cudaStream_t s) {
+  HalfSweep h{idx, wgt, norm, &plan, 0, 0, nullptr, false};
+  return run_half<float>(h, src, self_in, out, d, keep, scale, partials, s);
+}
+
+namespace {
 
 int ensure_scratch(float** p, size_t* have, size_t need, cudaStream_t s) {
   if (need <= *have && *p) return HNV_OK;
