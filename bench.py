@@ -591,6 +591,103 @@ def run_autograd_study(args):
         "forward_ms": t_fwd, "forward_backward_ms": t_fb, "ratio": t_fb / t_fwd}))
 
 
+def run_batch_study(args):
+    """The batching workload (256 planted hypergraphs, 1K..100K nodes, d=64):
+    the V-cycle of every graph looped through the single-graph path (FP32 and
+    BF16) against the batched path (BF16 and FP32; direct launches, one
+    captured CUDA graph, autotuned row classes). Device-resident buffers,
+    CUDA-event timing on one stream; all variants give the same rows per
+    dtype (tests/test_gpu_batch.py checks that)."""
+    import torch
+    import paper_2103_09660_gb300 as H
+    from paper_2103_09660_gb300 import build as B
+    B.build()
+    specs = hypergen.batch_specs(args.batch_count)
+    t0 = time.time()
+    hgs = [hypergen.generate(sp) for sp in specs]
+    t_gen = time.time() - t0
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    Gs = []
+    t0 = time.time()
+    for sp, hg in zip(specs, hgs):
+        G = H.Graph.from_hypergraph(hg, stream=stream)
+        G.coarsen(min_nodes=sp.min_nodes, max_levels=sp.max_levels, seed=sp.seed)
+        Gs.append(G)
+    torch.cuda.synchronize()
+    t_build = time.time() - t0
+    d, om, k = specs[0].d, 0.5, specs[0].sweeps
+    updates = 0
+    for G in Gs:
+        for lv in range(G.num_levels):
+            n, m, _ = G.level_info(lv)
+            updates += (n + m) * k
+    bat = H.Batch(Gs)
+    co, vo, eo = bat.offsets()
+    zc32 = torch.cat([torch.from_numpy(hypergen.coarsest_embedding(
+        int(co[i + 1] - co[i]), d, seed=specs[i].seed)) for i in range(len(Gs))]).to(dev)
+    bufs = {}
+    for name, dt in (("f32", torch.float32), ("bf16", torch.bfloat16)):
+        bufs[name] = (zc32.to(dt), torch.empty((int(vo[-1]), d), dtype=dt, device=dev),
+                      torch.empty((int(eo[-1]), d), dtype=dt, device=dev))
+
+    def loop(name):
+        zc, zv, ze = bufs[name]
+        for i, G in enumerate(Gs):
+            H.hnv_vcycle(G.handle, zc[co[i]:co[i + 1]], zv[vo[i]:vo[i + 1]], ze[eo[i]:eo[i + 1]],
+                         om, k, H.SWEEP_TWO_PHASE, stream)
+
+    def batched(name, graph):
+        zc, zv, ze = bufs[name]
+        return lambda: bat.vcycle(zc, zv, ze, om, k, use_cuda_graph=graph)
+
+    def timed(fn):
+        for _ in range(max(args.warmup, 1)):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            l0 = H.kernel_launch_count()
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return {"ms": float(np.median(ts)), "updates_per_s": updates / (np.median(ts) / 1e3),
+                "launches": int(H.kernel_launch_count() - l0)}
+
+    res = {}
+    res["loop_f32"] = timed(lambda: loop("f32"))
+    res["loop_bf16"] = timed(lambda: loop("bf16"))
+    res["batched_f32_direct"] = timed(batched("f32", False))
+    res["batched_f32_graph"] = timed(batched("f32", True))
+    res["batched_bf16_direct"] = timed(batched("bf16", False))
+    res["batched_bf16_graph"] = timed(batched("bf16", True))
+    t0 = time.time()
+    tune = bat.autotune(H.BF16, d, om)
+    t_tune = time.time() - t0
+    res["batched_bf16_graph_tuned"] = timed(batched("bf16", True))
+    tune32 = bat.autotune(H.F32, d, om)
+    res["batched_f32_graph_tuned"] = timed(batched("f32", True))
+    levels = [G.num_levels for G in Gs]
+    for G in Gs:
+        G.sync_status()
+    bat.close()
+    for G in Gs:
+        G.close()
+    print(json.dumps({
+        "study": "batched V-cycle vs looping the single-graph path",
+        "graphs": len(Gs), "nodes": int(vo[-1]), "hyperedges": int(eo[-1]),
+        "incidences": int(sum(h.nnz for h in hgs)), "d": d, "sweeps_per_level": k,
+        "levels_min": min(levels), "levels_max": max(levels),
+        "updates_per_vcycle": updates, "results": res,
+        "speedup_batched_bf16_tuned_vs_loop_f32":
+            res["loop_f32"]["ms"] / res["batched_bf16_graph_tuned"]["ms"],
+        "tuning_bf16": tune, "tuning_f32": tune32, "autotune_s": t_tune,
+        "generate_s": t_gen, "build_coarsen_s": t_build}))
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -606,6 +703,9 @@ def main(argv=None):
                     help="embedding storage of the timed V-cycle (sums are float32 either way)")
     ap.add_argument("--precision-study", action="store_true",
                     help="BF16 vs FP32 per level and V-cycle time (use with --workload planted_4m)")
+    ap.add_argument("--batch-study", action="store_true",
+                    help="batched V-cycle over many hypergraphs vs looping the single-graph path")
+    ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--autograd-study", action="store_true",
                     help="forward+backward vs forward time (use with --workload diff_200k)")
     args = ap.parse_args(argv)
@@ -618,6 +718,9 @@ def main(argv=None):
         return
     if args.autograd_study:
         run_autograd_study(args)
+        return
+    if args.batch_study:
+        run_batch_study(args)
         return
     if args.impl == "reference":
         line = run_reference(args, ws, rank, local)

@@ -38,7 +38,7 @@ against nothing else), so the library's own incidence build does the sort.
 from __future__ import annotations
 
 import dataclasses
-from typing import Dict, Optional
+from typing import Dict, List, Optional
 
 import numpy as np
 
@@ -114,6 +114,22 @@ CONFIGS: Dict[str, GenSpec] = {
                          cap=5_000, p_in=0.7, weighted=True, d=64, sweeps=10,
                          min_nodes=0, max_levels=3),
 }
+
+
+def batch_specs(count: int = 256, n_min: int = 1_000, n_max: int = 100_000,
+                seed: int = 0) -> List[GenSpec]:
+    """The batching workload: ``count`` independent planted-community
+    hypergraphs, node counts log-uniform in [n_min, n_max] (seeded), 0.8 n
+    hyperedges of size 2+Zipf(2.0) capped at 500, 8 communities, p_in 0.8,
+    unit weights, d = 64, 10 sweeps per level, each coarsened down to
+    max(200, n / 100) nodes."""
+    rng = np.random.default_rng([seed, 0xBA7C4])
+    ns = np.exp(rng.uniform(np.log(n_min), np.log(n_max), count)).astype(np.int64)
+    return [GenSpec("batch_%d" % i, n=int(n), m=int(0.8 * n), C=8, alpha=2.0, cap=500,
+                    p_in=0.8, weighted=False, d=64, sweeps=10,
+                    min_nodes=max(200, int(n) // 100), max_levels=32,
+                    seed=seed * 1_000_003 + i + 1)
+            for i, n in enumerate(ns)]
 
 
 def _first_occurrences(keys: np.ndarray) -> np.ndarray:

@@ -179,7 +179,12 @@ int hnv_project(const hnv_graph* g, int fine_level, const void* zc_v, const void
  *   z~_v = sum_{e ∋ v} w_e z_e / sum_{e ∋ v} w_e,
  *   z <- (1 - omega) z + omega z~,
  * in the given update order; rows with no neighbours are left unchanged.
- * Sums are float32 in a fixed order (results are deterministic).
+ * Sums are float32 in a fixed order (results are deterministic). Where one
+ * side's neighbour table (rows x d x element size) is far larger than L2,
+ * that side's long rows are summed in pieces, one per range of neighbour
+ * IDs (panels), and the pieces added in order: the first call for a new
+ * row size builds that plan (allocating; HNV_PANELS=<k> in the environment
+ * forces k panels).
  *   z_v [n_l x d], z_e [m_l x d] : device, read and written
  *   omega in [0, 1]; sweeps >= 0
  * ------------------------------------------------------------------------- */
@@ -219,6 +224,9 @@ int hnv_vcycle(hnv_graph* g, const void* z_coarsest, void* z_v_out, void* z_e_ou
  *   Returns HNV_ERR_TOO_LARGE when the level needs more scratch than the
  *   array holds: max(chunks of either half-sweep) * d * 4 bytes, where a row
  *   with more than 128 incidences contributes ceil(len / 128) chunks.
+ *   It always uses the regular row plan (building a panel plan would
+ *   allocate): on a level where hnv_refine cuts rows into panels the two
+ *   agree to float32 rounding, elsewhere bit for bit.
  *   The first call on a device looks up the array's device address (once per
  *   device, under a lock). All calls share the one array and it keeps the
  *   last call's contents; calls whose kernels overlap on the GPU (other
@@ -267,6 +275,55 @@ int hnv_vcycle_save(hnv_graph* g, const float* z_coarsest, float* z_v_out, float
 int hnv_vcycle_backward(hnv_graph* g, const float* checkpoints, const float* g_v0,
                         const float* g_e0, float* grad_w0, float* grad_z_coarsest, int d,
                         float omega, int sweeps_per_level, hnv_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched V-cycle: many independent hypergraphs refined together
+ *
+ * Each graph is built and coarsened as usual (its hierarchy does not change).
+ * The batch lines the graphs up by level index: at step s (deepest level
+ * first) every graph whose coarsest level is >= s projects onto its level s
+ * (or starts from its input rows at its coarsest level) and runs the
+ * two-phase sweeps of Algorithm 2 there. Per half-sweep, one launch per row
+ * class covers the rows of all graphs (a work list with a graph index per
+ * item); the whole V-cycle can be captured once into a CUDA graph and
+ * replayed. Results equal hnv_vcycle on each graph (same per-row sums).
+ * ------------------------------------------------------------------------- */
+typedef struct hnv_batch hnv_batch;
+
+/* Row-length classes and lanes per row chosen by hnv_batch_autotune. */
+typedef struct {
+  int32_t a_max, b_max, c_max;          /* class boundaries (incidences) */
+  int32_t lanes_a, lanes_b, lanes_rest; /* lanes per row of the classes  */
+  float best_ms;                        /* one level-0 sweep, ms (-1: cached) */
+  int32_t from_cache;                   /* 1: taken from the tuning cache */
+} hnv_batch_tuning;
+
+/* A batch over `count` graphs (built and coarsened; all on one device). The
+ * batch references the graphs (they must outlive it) and owns its own work
+ * lists, buffers, stream and captured graph. */
+int hnv_batch_create(hnv_graph* const* graphs, int32_t count, hnv_batch** out);
+
+/* Row offsets of the batched buffers (each array count + 1 entries, host):
+ * graph i's coarsest rows (its nodes, then its hyperedges) start at row
+ * coarsest_rows[i] of z_coarsest; its level-0 node rows at node_rows[i] of
+ * z_v_out; its level-0 hyperedge rows at edge_rows[i] of z_e_out. */
+int hnv_batch_offsets(const hnv_batch* b, int64_t* coarsest_rows, int64_t* node_rows,
+                      int64_t* edge_rows);
+
+/* Times candidate row-class boundaries and lanes per row on one level-0 sweep
+ * of the batch and keeps the fastest (cached per dtype, d and the batch's
+ * level-0 row-length histogram). Synchronises. */
+int hnv_batch_autotune(hnv_batch* b, hnv_dtype dt, int d, float omega, hnv_batch_tuning* chosen);
+
+/* The two-phase V-cycle of every graph of the batch (device buffers laid out
+ * as hnv_batch_offsets says; d % 8 == 0). With use_cuda_graph the whole
+ * cycle is captured once (per buffers, dtype, d, omega and sweeps) and
+ * replayed on `stream`. */
+int hnv_batch_vcycle(hnv_batch* b, const void* z_coarsest, void* z_v_out, void* z_e_out,
+                     hnv_dtype dt, int d, float omega, int sweeps_per_level, int use_cuda_graph,
+                     hnv_stream_t stream);
+
+void hnv_batch_free(hnv_batch* b);
 
 /* Synchronises `stream` and reports device-side failures of the graph's
  * asynchronous calls since the last check: HNV_ERR_TIMEOUT if a bounded

@@ -29,7 +29,7 @@ __all__ = [
     "PHASE_BUILD", "PHASE_COARSEN", "PHASE_PROJECT", "PHASE_REFINE_E", "PHASE_REFINE_V",
     "Graph", "hnv_build_incidence", "hnv_coarsen", "hnv_project", "hnv_refine",
     "hnv_vcycle", "hnv_refine_noalloc", "hnv_set_weights", "hnv_checkpoint_floats",
-    "hnv_vcycle_save", "hnv_vcycle_backward", "vcycle_autograd", "kernel_launch_count", "timing_enable", "timing_reset", "timing_read",
+    "hnv_vcycle_save", "hnv_vcycle_backward", "vcycle_autograd", "Batch", "kernel_launch_count", "timing_enable", "timing_reset", "timing_read",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -66,6 +66,13 @@ class CoarsenParams(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("explicit_prio", ctypes.c_void_p)]
 
 
+class BatchTuning(ctypes.Structure):
+    _fields_ = [("a_max", ctypes.c_int32), ("b_max", ctypes.c_int32), ("c_max", ctypes.c_int32),
+                ("lanes_a", ctypes.c_int32), ("lanes_b", ctypes.c_int32),
+                ("lanes_rest", ctypes.c_int32), ("best_ms", ctypes.c_float),
+                ("from_cache", ctypes.c_int32)]
+
+
 _lib = None
 _P = ctypes.c_void_p
 
@@ -85,6 +92,11 @@ def _declare(L):
         "hnv_refine_noalloc": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_int, f32, ctypes.c_int, _P]),
         "hnv_graph_free": (None, [_P]),
         "hnv_sync_status": (ctypes.c_int, [_P, _P]),
+        "hnv_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), i32, ctypes.POINTER(_P)]),
+        "hnv_batch_offsets": (ctypes.c_int, [_P, _P, _P, _P]),
+        "hnv_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, f32, ctypes.POINTER(BatchTuning)]),
+        "hnv_batch_vcycle": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_int, f32, ctypes.c_int, ctypes.c_int, _P]),
+        "hnv_batch_free": (None, [_P]),
         "hnv_set_weights": (ctypes.c_int, [_P, _P, ctypes.c_int, _P]),
         "hnv_checkpoint_floats": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(i64)]),
         "hnv_vcycle_save": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, f32, ctypes.c_int, _P, _P]),
@@ -455,3 +467,59 @@ class Graph:
 
     def vcycle(self, z_coarsest, z_v_out, z_e_out, omega=0.5, sweeps=10, mode=SWEEP_TWO_PHASE):
         hnv_vcycle(self.handle, z_coarsest, z_v_out, z_e_out, omega, sweeps, mode, self.stream)
+
+
+class Batch:
+    """Many hypergraphs refined together (hnv_batch_*): one launch per row
+    class and half-sweep covers every graph, the V-cycle is captured into a
+    CUDA graph. The graphs must stay alive while the batch is used."""
+
+    def __init__(self, graphs):
+        self.graphs = list(graphs)
+        arr = (_P * len(self.graphs))(*[g.handle for g in self.graphs])
+        out = _P()
+        _check(lib().hnv_batch_create(arr, len(self.graphs), ctypes.byref(out)), "hnv_batch_create")
+        self.handle = out.value
+        self.stream = self.graphs[0].stream
+        self._rows = tuple(int(a[-1]) for a in self.offsets())
+
+    def offsets(self):
+        """(coarsest, node, hyperedge) row offsets, each count + 1 int64."""
+        k = len(self.graphs) + 1
+        a, b, c = (np.empty(k, np.int64) for _ in range(3))
+        _check(lib().hnv_batch_offsets(self.handle, a.ctypes.data, b.ctypes.data, c.ctypes.data),
+               "hnv_batch_offsets")
+        return a, b, c
+
+    def autotune(self, dtype: int, d: int, omega: float = 0.5) -> dict:
+        t = BatchTuning()
+        _check(lib().hnv_batch_autotune(self.handle, dtype, int(d), float(omega), ctypes.byref(t)),
+               "hnv_batch_autotune")
+        return {f: getattr(t, f) for f, _ in BatchTuning._fields_}
+
+    def vcycle(self, z_coarsest, z_v_out, z_e_out, omega=0.5, sweeps=10, use_cuda_graph=True):
+        dt, tdt = _emb_dtype(z_coarsest)
+        d = z_coarsest.shape[1]
+        rc, rv, re = self._rows
+        _check(lib().hnv_batch_vcycle(self.handle, _dev_ptr(z_coarsest, tdt, "z_coarsest", rc, d),
+                                      _dev_ptr(z_v_out, tdt, "z_v_out", rv, d),
+                                      _dev_ptr(z_e_out, tdt, "z_e_out", re, d), dt, int(d), float(omega),
+                                      int(sweeps), 1 if use_cuda_graph else 0,
+                                      _stream_handle(self.stream)), "hnv_batch_vcycle")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().hnv_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

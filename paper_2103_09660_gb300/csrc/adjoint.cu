@@ -228,7 +228,7 @@ int prepare_level_adjoint(hnv_graph* g, int level, cudaStream_t s) {
   HNV_CHECK(launch("key_counts", key_counts, grid_for(total, 256), 256, 0, s,
                    (const uint64_t*)sorted, total, cnt, lv.ch_idx));
   HNV_CHECK(exclusive_scan_i32(cnt, lv.ch_ptr, (int64_t)n_c + 1, nullptr, s));
-  HNV_CHECK(build_split_plan(g, &lv, lv.ch_ptr, n_c, &lv.planC, s));
+  HNV_CHECK(build_split_plan(g, &lv.owned, lv.ch_ptr, n_c, &lv.planC, s));
   lv.adj_ready = true;
   return HNV_OK;
 }

@@ -493,6 +493,8 @@ int hnv_sync_status(hnv_graph* g, hnv_stream_t stream) {
   HNV_CHECK(read_and_clear_err(g, s, &bits));
   if (bits & ERRBIT_TIMEOUT)
     HNV_FAIL(HNV_ERR_TIMEOUT, "a bounded wait of a refinement kernel gave up");
+  if (bits & ERRBIT_BAD_ITEM)
+    HNV_FAIL(HNV_ERR_STATE, "a batched work item lay outside its graph's arrays and was skipped");
   return HNV_OK;
 }
 

@@ -1,0 +1,927 @@
+// Batched V-cycle: many independent hypergraphs refined together.
+//
+// Every graph keeps its own hierarchy (built and coarsened as usual). The
+// batch lines the graphs up by level index: at step s (from the deepest
+// level down to 0) every graph whose coarsest level is >= s projects onto
+// level s (or, at its own coarsest level, starts from its input rows) and
+// refines it. The work of one half-sweep of one step, over all graphs, is a
+// single list of items {row, first incidence, length, partial slot} with a
+// graph index per item; batched_gather_kernel runs the same per-item gather
+// as the single-graph path (refine_device.cuh) with that graph's pointers,
+// looping over the list with a grid of a few blocks per SM. One launch per
+// row class and side replaces one launch per class, side and graph; the
+// whole V-cycle (all steps, sweeps, projections) is captured once into a
+// CUDA graph and replayed.
+//
+// Autotuner: the row-class boundaries (PlanShape) and the lanes per row of
+// the short classes are chosen by timing candidate settings on the batch's
+// level 0, and cached per (dtype, d, level-0 length histogram).
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "refine_device.cuh"
+
+namespace hnv {
+
+namespace {
+
+// HNV_TRACE=1: host-side progress of the batch calls on stderr.
+bool trace_on() {
+  static int on = -1;
+  if (on < 0) {
+    const char* e = getenv("HNV_TRACE");
+    on = (e && e[0] == '1') ? 1 : 0;
+  }
+  return on == 1;
+}
+
+#define BTRACE(...)                        \
+  do {                                     \
+    if (trace_on()) {                      \
+      fprintf(stderr, "[hnv_batch] ");     \
+      fprintf(stderr, __VA_ARGS__);        \
+      fprintf(stderr, "\n");               \
+      fflush(stderr);                      \
+    }                                      \
+  } while (0)
+
+struct GraphSide {
+  const int32_t* idx;
+  const float* inc_w;
+  const float* inv_norm;
+  const uint4* src;
+  const uint4* self_in;
+  uint4* out;
+  float* partials;
+  // bounds every item of this graph must respect (checked per item; an item
+  // outside them is skipped and flagged in err)
+  int32_t self_rows = 0;
+  int64_t nnz = 0;
+  int64_t n_slots = 0;
+  int32_t* err = nullptr;
+};
+
+struct ProjDesc {
+  const int32_t* rep_v;
+  const int32_t* rep_e;
+  int32_t n_f, m_f;
+  const uint4* zc_v;
+  const uint4* zc_e;
+  uint4* zf_v;
+  uint4* zf_e;
+};
+
+struct CopyDesc {
+  const uint4* src;
+  uint4* dst;
+};
+
+template <typename T, int G, int VPL, bool W>
+__global__ void __launch_bounds__(256)
+batched_gather_kernel(const int4* __restrict__ items, const int32_t* __restrict__ item_g,
+                      int32_t n_items, const GraphSide* __restrict__ sides, int32_t n_graphs,
+                      int32_t dv, float keep, float scale) {
+  constexpr int R = 32 / G;
+  const int lane = threadIdx.x & 31;
+  const int grp = lane / G;
+  const int lg = lane & (G - 1);
+  const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t wbase = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * R;
+       wbase < n_items; wbase += warps_total * R) {
+    const int64_t item = wbase + grp;
+    int4 it = make_int4(-1, 0, 0, -1);
+    int32_t gi = 0;
+    bool bad = false;
+    if (item < n_items) {
+      it = __ldg(items + item);
+      gi = __ldg(item_g + item);
+      if (gi < 0 || gi >= n_graphs) {
+        gi = 0;
+        bad = true;
+      }
+    }
+    const GraphSide sd = sides[gi];
+    if (item < n_items) {
+      bad = bad || it.x < -1 || it.x >= sd.self_rows || it.y < 0 || it.z < 0 ||
+            (int64_t)it.y + it.z > sd.nnz || it.w >= sd.n_slots || (it.x < 0 && it.w < 0);
+      if (bad) {
+        if (sd.err) atomicOr(sd.err, (int32_t)ERRBIT_BAD_ITEM);
+        it = make_int4(-1, 0, 0, -1);
+      }
+    }
+    dev::gather_item<T, G, VPL, W>(it, lg, sd.idx, sd.inc_w, sd.inv_norm, sd.src, sd.self_in,
+                                   sd.out, dv, keep, scale, sd.partials);
+  }
+}
+
+constexpr int kFinThreads = 1024;
+
+template <typename T>
+__global__ void __launch_bounds__(kFinThreads)
+batched_finalize_kernel(const int4* __restrict__ long_desc, const int32_t* __restrict__ long_g,
+                        int32_t n_mid, int32_t n_huge, int32_t mid_blocks,
+                        const GraphSide* __restrict__ sides, int32_t n_graphs, int32_t dv,
+                        float keep, float scale) {
+  extern __shared__ float4 sm4[];
+  const bool mid = (int32_t)blockIdx.x < mid_blocks;
+  const int32_t k = mid ? (int32_t)(blockIdx.x * (kFinThreads / 32) + (threadIdx.x >> 5))
+                        : n_mid + (int32_t)blockIdx.x - mid_blocks;
+  if (k >= (mid ? n_mid : n_mid + n_huge)) return;
+  const int32_t gi = long_g[k];
+  if (gi < 0 || gi >= n_graphs) return;   // (cannot be flagged without a graph)
+  const GraphSide sd = sides[gi];
+  const int4 ds = long_desc[k];
+  // self-check: the row and its chunk run must lie inside the graph's arrays
+  if (ds.x < 0 || ds.x >= sd.self_rows || ds.z < 1 || ds.y < 0 ||
+      (int64_t)ds.y + ds.z > sd.n_slots || (mid && ds.z > kMidChunks)) {
+    if (sd.err && (threadIdx.x & 31) == 0) atomicOr(sd.err, (int32_t)ERRBIT_BAD_ITEM);
+    return;   // uniform per warp (mid) or per block (huge)
+  }
+  if (mid) {
+    dev::finalize_mid<T>(ds, threadIdx.x & 31, sd.partials, sd.inv_norm, sd.self_in, sd.out, dv,
+                         keep, scale);
+    return;
+  }
+  dev::finalize_huge<T>(ds, reinterpret_cast<float*>(sm4), sd.partials, sd.inv_norm, sd.self_in,
+                        sd.out, dv, keep, scale);
+}
+
+// index of the segment of `prefix` (n+1 ascending offsets) holding i
+__device__ __forceinline__ int32_t segment_of(const int64_t* __restrict__ prefix, int32_t n,
+                                              int64_t i) {
+  int32_t lo = 0, hi = n;   // prefix[lo] <= i < prefix[hi]
+  while (hi - lo > 1) {
+    const int32_t mid = (lo + hi) >> 1;
+    if (prefix[mid] <= i) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void batched_project_kernel(const ProjDesc* __restrict__ pd,
+                                       const int64_t* __restrict__ prefix, int32_t n,
+                                       int64_t total, int32_t dv) {
+  if (prefix[n] != total) return;   // self-check: the table is the one the host built
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t g = segment_of(prefix, n, i);
+    const ProjDesc p = pd[g];
+    const int64_t local = i - prefix[g];
+    const int64_t row = local / dv;
+    const int32_t col = (int32_t)(local - row * dv);
+    if (row < p.n_f) {
+      p.zf_v[local] = p.zc_v[(size_t)p.rep_v[row] * dv + col];
+    } else {
+      const int64_t e = row - p.n_f;
+      const int32_t r = p.rep_e[e];
+      const uint4* s = (r >= 0) ? p.zc_e + (size_t)r * dv : p.zc_v + (size_t)(-1 - r) * dv;
+      p.zf_e[e * dv + col] = s[col];
+    }
+  }
+}
+
+__global__ void batched_copy_kernel(const CopyDesc* __restrict__ cd,
+                                    const int64_t* __restrict__ prefix, int32_t n,
+                                    int64_t total) {
+  if (prefix[n] != total) return;   // self-check: the table is the one the host built
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t g = segment_of(prefix, n, i);
+    cd[g].dst[i - prefix[g]] = cd[g].src[i - prefix[g]];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+
+struct BSide {
+  int4* items = nullptr;
+  int32_t* item_g = nullptr;
+  int32_t n_cls[3] = {0, 0, 0};   // A rows, B rows, the rest (C, D rows and chunks)
+  int4* long_desc = nullptr;
+  int32_t* long_g = nullptr;
+  int32_t n_mid = 0, n_huge = 0;
+  GraphSide* sides = nullptr;     // device, indexed by graph
+  int32_t n_graphs = 0;
+  bool weighted = false;
+};
+
+struct BStep {
+  BSide side[2];                  // 0: hyperedge rows, 1: node rows
+  ProjDesc* proj = nullptr;
+  int64_t* proj_prefix = nullptr;
+  int32_t n_proj = 0;
+  CopyDesc* copies = nullptr;
+  int64_t* copy_prefix = nullptr;
+  int32_t n_copies = 0;
+  int64_t proj_total = 0, copy_total = 0;   // vectors to move
+};
+
+int next_pow2(int x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+}  // namespace
+}  // namespace hnv
+
+using namespace hnv;
+
+struct hnv_batch {
+  std::vector<hnv_graph*> graphs;
+  int device = 0;
+  cudaStream_t cap_stream = nullptr;
+  std::vector<int> top;            // coarsest level of each graph
+  int Lmax = 0;
+  PlanShape shape;
+  int lanes[3] = {0, 0, 0};        // lanes per row of classes A, B, rest (0: default)
+  // per-graph plans for `shape`: plans[side][graph][level]
+  std::vector<std::vector<SplitPlan>> plans[2];
+  std::vector<void*> plan_owned;
+  bool plans_ready = false;
+  size_t plans_row_bytes = 0;
+  // step structures for one (dtype, d, buffers)
+  std::vector<BStep> steps;
+  std::vector<void*> step_owned;
+  float* partials = nullptr;
+  uint8_t* arena[2] = {nullptr, nullptr};
+  int built_dt = -1, built_d = -1;
+  const void* built_zc = nullptr;
+  const void* built_zv = nullptr;
+  const void* built_ze = nullptr;
+  // captured V-cycle
+  cudaGraphExec_t exec = nullptr;
+  float exec_omega = -1.f;
+  int exec_sweeps = -1;
+  int64_t exec_kernels = 0;        // kernel nodes of the captured V-cycle
+  std::vector<int64_t> coarse_off, v_off, e_off;   // row offsets (count + 1)
+};
+
+namespace hnv {
+namespace {
+
+std::mutex g_tune_mu;
+std::map<std::vector<int64_t>, std::pair<PlanShape, std::vector<int>>> g_tune_cache;
+
+void free_list(std::vector<void*>& v, cudaStream_t s) {
+  for (void* p : v) dev_free(p, s);
+  v.clear();
+}
+
+int alloc_into(std::vector<void*>& owned, void** p, size_t bytes, cudaStream_t s) {
+  HNV_CHECK(dev_alloc(p, bytes ? bytes : 16, s));
+  owned.push_back(*p);
+  return HNV_OK;
+}
+
+// Row-class plans of every graph and level. Where the single-graph path
+// cuts long rows into panels (a neighbour table far larger than L2), the
+// batch builds the same panel plan from the level's own regular plan, so
+// both sum every row in the same order; elsewhere it uses its tuned shape.
+int build_plans(hnv_batch* b, size_t row_bytes, cudaStream_t s, int only_level = -1) {
+  BTRACE("build_plans row_bytes=%zu only_level=%d", row_bytes, only_level);
+  free_list(b->plan_owned, s);
+  for (int side = 0; side < 2; ++side) b->plans[side].assign(b->graphs.size(), {});
+  for (size_t i = 0; i < b->graphs.size(); ++i) {
+    hnv_graph* g = b->graphs[i];
+    const int L = (int)g->levels.size();
+    for (int side = 0; side < 2; ++side) b->plans[side][i].assign(L, SplitPlan());
+    for (int l = 0; l < L; ++l) {
+      if (only_level >= 0 && l != only_level) continue;
+      Level& lv = g->levels[l];
+      for (int side = 0; side < 2; ++side) {
+        const int32_t rows = side == 0 ? lv.m : lv.n, cols = side == 0 ? lv.n : lv.m;
+        const int32_t* ptr = side == 0 ? lv.e_ptr : lv.v_ptr;
+        SplitPlan& out = b->plans[side][i][l];
+        int P = 1;
+        if (rows > 0 && cols > 0)
+          HNV_CHECK(build_panel_plan(g, &b->plan_owned, side == 0 ? lv.planE : lv.planV, ptr,
+                                     side == 0 ? lv.e_nodes : lv.v_edges, cols,
+                                     (int64_t)cols * (int64_t)row_bytes, &out, &P, s));
+        if (P <= 1) HNV_CHECK(build_split_plan(g, &b->plan_owned, ptr, rows, &out, s, b->shape));
+        BTRACE("plan graph %zu level %d side %d: P=%d a=%d b=%d c=%d d=%d chunks=%d mid=%d huge=%d",
+               i, l, side, P, out.n_a, out.n_b, out.n_c, out.n_d, out.n_chunks, out.n_mid,
+               out.n_huge);
+      }
+    }
+  }
+  b->plans_ready = only_level < 0;
+  b->plans_row_bytes = row_bytes;
+  return HNV_OK;
+}
+
+void free_steps(hnv_batch* b, cudaStream_t s) {
+  free_list(b->step_owned, s);
+  b->steps.clear();
+  b->partials = nullptr;
+  b->arena[0] = b->arena[1] = nullptr;
+  b->built_dt = b->built_d = -1;
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+}
+
+// Work lists, pointer tables and buffers of every step for (dt, d) and the
+// caller's buffers. `only_step` >= 0 builds that step only (the autotuner
+// times step 0).
+int build_steps(hnv_batch* b, int dt, int d, const uint8_t* zc, uint8_t* zv0, uint8_t* ze0,
+                cudaStream_t s, int only_step = -1) {
+  BTRACE("build_steps dt=%d d=%d only_step=%d Lmax=%d", dt, d, only_step, b->Lmax);
+  free_steps(b, s);
+  const size_t rb = (dt == HNV_BF16 ? 2 : 4) * (size_t)d;
+  const int32_t dv = (int32_t)(rb / 16);
+  const size_t G = b->graphs.size();
+  b->steps.assign(b->Lmax + 1, BStep());
+  // arenas for levels >= 1 (parity of the level)
+  size_t arena_rows = 0;
+  for (int st = 1; st <= b->Lmax; ++st) {
+    size_t rows = 0;
+    for (size_t i = 0; i < G; ++i)
+      if (b->top[i] >= st) rows += (size_t)b->graphs[i]->levels[st].n + b->graphs[i]->levels[st].m;
+    arena_rows = std::max(arena_rows, rows);
+  }
+  if (arena_rows > 0 && only_step != 0) {
+    HNV_CHECK(alloc_into(b->step_owned, (void**)&b->arena[0], arena_rows * rb, s));
+    HNV_CHECK(alloc_into(b->step_owned, (void**)&b->arena[1], arena_rows * rb, s));
+  }
+  // row pointers of graph i at level st
+  std::vector<std::vector<uint8_t*>> zvp(b->Lmax + 1, std::vector<uint8_t*>(G, nullptr));
+  std::vector<std::vector<uint8_t*>> zep = zvp;
+  for (int st = 0; st <= b->Lmax; ++st) {
+    size_t off = 0;
+    for (size_t i = 0; i < G; ++i) {
+      if (b->top[i] < st) continue;
+      const Level& lv = b->graphs[i]->levels[st];
+      if (st == 0) {
+        zvp[st][i] = zv0 + (size_t)b->v_off[i] * rb;
+        zep[st][i] = ze0 + (size_t)b->e_off[i] * rb;
+      } else {
+        zvp[st][i] = b->arena[st & 1] + off * rb;
+        zep[st][i] = zvp[st][i] + (size_t)lv.n * rb;
+        off += (size_t)lv.n + lv.m;
+      }
+    }
+  }
+  // partials: the largest step-side total
+  size_t max_chunks = 1;
+  for (int st = 0; st <= b->Lmax; ++st)
+    for (int side = 0; side < 2; ++side) {
+      size_t c = 0;
+      for (size_t i = 0; i < G; ++i)
+        if (b->top[i] >= st) c += b->plans[side][i][st].n_chunks;
+      max_chunks = std::max(max_chunks, c);
+    }
+  HNV_CHECK(alloc_into(b->step_owned, (void**)&b->partials, max_chunks * sizeof(float) * d, s));
+
+  for (int st = 0; st <= b->Lmax; ++st) {
+    if (only_step >= 0 && st != only_step) continue;
+    BStep& S = b->steps[st];
+    for (int side = 0; side < 2; ++side) {
+      BSide& B = S.side[side];
+      B.weighted = side == 1;
+      std::vector<GraphSide> hs(G);
+      B.n_graphs = (int32_t)G;
+      int64_t n_items = 0, n_long = 0, chunk_base = 0;
+      for (size_t i = 0; i < G; ++i) {
+        if (b->top[i] < st) continue;
+        const Level& lv = b->graphs[i]->levels[st];
+        const SplitPlan& p = b->plans[side][i][st];
+        GraphSide& gs = hs[i];
+        if (side == 0) {
+          gs.idx = lv.e_nodes;
+          gs.inc_w = nullptr;
+          gs.inv_norm = lv.inv_size_e;
+          gs.src = (const uint4*)zvp[st][i];
+          gs.self_in = (const uint4*)zep[st][i];
+          gs.out = (uint4*)zep[st][i];
+          gs.self_rows = lv.m;
+        } else {
+          gs.idx = lv.v_edges;
+          gs.inc_w = lv.v_w;
+          gs.inv_norm = lv.inv_deg_v;
+          gs.src = (const uint4*)zep[st][i];
+          gs.self_in = (const uint4*)zvp[st][i];
+          gs.out = (uint4*)zvp[st][i];
+          gs.self_rows = lv.n;
+        }
+        gs.nnz = lv.nnz;
+        gs.n_slots = p.n_chunks;
+        gs.err = b->graphs[i]->d_err;
+        gs.partials = b->partials + (size_t)chunk_base * d;
+        chunk_base += p.n_chunks;
+        n_items += (int64_t)p.n_a + p.n_b + p.n_c + p.n_d + p.n_chunks;
+        n_long += (int64_t)p.n_mid + p.n_huge;
+      }
+      HNV_CHECK(alloc_into(b->step_owned, (void**)&B.sides, sizeof(GraphSide) * G, s));
+      HNV_CUDA(cudaMemcpyAsync(B.sides, hs.data(), sizeof(GraphSide) * G, cudaMemcpyHostToDevice, s));
+      HNV_CHECK(alloc_into(b->step_owned, (void**)&B.items, sizeof(int4) * (size_t)n_items, s));
+      HNV_CHECK(alloc_into(b->step_owned, (void**)&B.item_g, sizeof(int32_t) * (size_t)n_items, s));
+      HNV_CHECK(alloc_into(b->step_owned, (void**)&B.long_desc, sizeof(int4) * (size_t)n_long, s));
+      HNV_CHECK(alloc_into(b->step_owned, (void**)&B.long_g, sizeof(int32_t) * (size_t)n_long, s));
+      std::vector<int32_t> hg_items, hg_long;
+      hg_items.reserve(n_items);
+      hg_long.reserve(n_long);
+      int64_t pos = 0;
+      for (int cls = 0; cls < 3; ++cls) {
+        int64_t cls_count = 0;
+        for (size_t i = 0; i < G; ++i) {
+          if (b->top[i] < st) continue;
+          const SplitPlan& p = b->plans[side][i][st];
+          int64_t first = 0, count = 0;
+          if (cls == 0) { first = 0; count = p.n_a; }
+          else if (cls == 1) { first = p.n_a; count = p.n_b; }
+          else { first = (int64_t)p.n_a + p.n_b; count = (int64_t)p.n_c + p.n_d + p.n_chunks; }
+          if (count == 0) continue;
+          HNV_CUDA(cudaMemcpyAsync(B.items + pos, p.items + first, sizeof(int4) * count,
+                                   cudaMemcpyDeviceToDevice, s));
+          hg_items.insert(hg_items.end(), count, (int32_t)i);
+          pos += count;
+          cls_count += count;
+        }
+        B.n_cls[cls] = (int32_t)cls_count;
+      }
+      int64_t lpos = 0;
+      for (int part = 0; part < 2; ++part) {   // rows with few chunks first, then the rest
+        int64_t cnt_part = 0;
+        for (size_t i = 0; i < G; ++i) {
+          if (b->top[i] < st) continue;
+          const SplitPlan& p = b->plans[side][i][st];
+          const int64_t first = part == 0 ? 0 : p.n_mid;
+          const int64_t count = part == 0 ? p.n_mid : p.n_huge;
+          if (count == 0) continue;
+          HNV_CUDA(cudaMemcpyAsync(B.long_desc + lpos, p.long_desc + first, sizeof(int4) * count,
+                                   cudaMemcpyDeviceToDevice, s));
+          hg_long.insert(hg_long.end(), count, (int32_t)i);
+          lpos += count;
+          cnt_part += count;
+        }
+        if (part == 0) B.n_mid = (int32_t)cnt_part;
+        else B.n_huge = (int32_t)cnt_part;
+      }
+      if (n_items)
+        HNV_CUDA(cudaMemcpyAsync(B.item_g, hg_items.data(), sizeof(int32_t) * n_items,
+                                 cudaMemcpyHostToDevice, s));
+      if (n_long)
+        HNV_CUDA(cudaMemcpyAsync(B.long_g, hg_long.data(), sizeof(int32_t) * n_long,
+                                 cudaMemcpyHostToDevice, s));
+      HNV_CUDA(cudaStreamSynchronize(s));   // the host vectors above die here
+      BTRACE("step %d side %d: items %lld (A %d B %d rest %d) long %lld (mid %d huge %d)", st,
+             side, (long long)n_items, B.n_cls[0], B.n_cls[1], B.n_cls[2], (long long)n_long,
+             B.n_mid, B.n_huge);
+    }
+    // projections onto level st and starting rows at level st
+    std::vector<ProjDesc> pd;
+    std::vector<int64_t> ppre{0};
+    std::vector<CopyDesc> cd;
+    std::vector<int64_t> cpre{0};
+    for (size_t i = 0; i < G; ++i) {
+      if (b->top[i] < st) continue;
+      const Level& lv = b->graphs[i]->levels[st];
+      if (b->top[i] > st) {
+        pd.push_back(ProjDesc{lv.rep_v, lv.rep_e, lv.n, lv.m, (const uint4*)zvp[st + 1][i],
+                              (const uint4*)zep[st + 1][i], (uint4*)zvp[st][i],
+                              (uint4*)zep[st][i]});
+        ppre.push_back(ppre.back() + ((int64_t)lv.n + lv.m) * dv);
+      } else {
+        const uint8_t* src = zc + (size_t)b->coarse_off[i] * rb;
+        if (lv.n > 0) {
+          cd.push_back(CopyDesc{(const uint4*)src, (uint4*)zvp[st][i]});
+          cpre.push_back(cpre.back() + (int64_t)lv.n * dv);
+        }
+        if (lv.m > 0) {
+          cd.push_back(CopyDesc{(const uint4*)(src + (size_t)lv.n * rb), (uint4*)zep[st][i]});
+          cpre.push_back(cpre.back() + (int64_t)lv.m * dv);
+        }
+      }
+    }
+    S.n_proj = (int32_t)pd.size();
+    S.n_copies = (int32_t)cd.size();
+    S.proj_total = ppre.back();
+    S.copy_total = cpre.back();
+    if (S.n_proj) {
+      HNV_CHECK(alloc_into(b->step_owned, (void**)&S.proj, sizeof(ProjDesc) * pd.size(), s));
+      HNV_CHECK(alloc_into(b->step_owned, (void**)&S.proj_prefix, sizeof(int64_t) * ppre.size(), s));
+      HNV_CUDA(cudaMemcpyAsync(S.proj, pd.data(), sizeof(ProjDesc) * pd.size(), cudaMemcpyHostToDevice, s));
+      HNV_CUDA(cudaMemcpyAsync(S.proj_prefix, ppre.data(), sizeof(int64_t) * ppre.size(),
+                               cudaMemcpyHostToDevice, s));
+    }
+    if (S.n_copies) {
+      HNV_CHECK(alloc_into(b->step_owned, (void**)&S.copies, sizeof(CopyDesc) * cd.size(), s));
+      HNV_CHECK(alloc_into(b->step_owned, (void**)&S.copy_prefix, sizeof(int64_t) * cpre.size(), s));
+      HNV_CUDA(cudaMemcpyAsync(S.copies, cd.data(), sizeof(CopyDesc) * cd.size(), cudaMemcpyHostToDevice, s));
+      HNV_CUDA(cudaMemcpyAsync(S.copy_prefix, cpre.data(), sizeof(int64_t) * cpre.size(),
+                               cudaMemcpyHostToDevice, s));
+    }
+    HNV_CUDA(cudaStreamSynchronize(s));
+  }
+  b->built_dt = dt;
+  b->built_d = d;
+  return HNV_OK;
+}
+
+// lanes per row of class c (0: A, 1: B, 2: rest) for rows of dv vectors
+int class_lanes(const hnv_batch* b, int c, int dv) {
+  const int natural[3] = {8, 16, 32};
+  int g = b->lanes[c] > 0 ? b->lanes[c] : natural[c];
+  g = std::min(g, next_pow2(dv));
+  g = std::max(g, next_pow2((dv + 7) / 8));
+  return std::min(g, 32);
+}
+
+template <typename T, int G, int VPL, bool W>
+int launch_batched_items(const BSide& B, int64_t first, int32_t count, int dv, float keep,
+                         float scale, cudaStream_t s) {
+  if (count <= 0) return HNV_OK;
+  constexpr int R = 32 / G;
+  auto kern = batched_gather_kernel<T, G, VPL, W>;
+  int per_sm = 0;
+  HNV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0));
+  if (per_sm < 1) per_sm = 1;
+  const int64_t warps = ((int64_t)count + R - 1) / R;
+  int64_t blocks = (warps + 7) / 8;
+  blocks = std::min<int64_t>(blocks, (int64_t)num_sms() * per_sm);
+  BTRACE("launch gather G=%d VPL=%d W=%d first=%lld count=%d blocks=%lld per_sm=%d", G, VPL,
+         (int)W, (long long)first, count, (long long)blocks, per_sm);
+  return launch("batched_gather", kern, (unsigned)blocks, 256, 0, s,
+                (const int4*)(B.items + first), (const int32_t*)(B.item_g + first), count,
+                (const GraphSide*)B.sides, B.n_graphs, dv, keep, scale);
+}
+
+template <typename T, bool W>
+int launch_batched_dispatch(int G, int VPL, const BSide& B, int64_t first, int32_t count, int dv,
+                            float keep, float scale, cudaStream_t s) {
+#define HNV_BCASE(g, v)                                                                      \
+  if (G == g && VPL == v)                                                                    \
+    return launch_batched_items<T, g, v, W>(B, first, count, dv, keep, scale, s);
+  HNV_BCASE(1, 1) HNV_BCASE(2, 1) HNV_BCASE(2, 2) HNV_BCASE(2, 4) HNV_BCASE(2, 8)
+  HNV_BCASE(4, 1) HNV_BCASE(4, 2) HNV_BCASE(4, 4) HNV_BCASE(4, 8)
+  HNV_BCASE(8, 1) HNV_BCASE(8, 2) HNV_BCASE(8, 4) HNV_BCASE(8, 8)
+  HNV_BCASE(16, 1) HNV_BCASE(16, 2) HNV_BCASE(16, 4) HNV_BCASE(16, 8)
+  HNV_BCASE(32, 1) HNV_BCASE(32, 2) HNV_BCASE(32, 4) HNV_BCASE(32, 8)
+#undef HNV_BCASE
+  HNV_FAIL(HNV_ERR_UNSUPPORTED_D, "no batched gather variant for G=%d VPL=%d", G, VPL);
+}
+
+template <typename T>
+int enqueue_half(const hnv_batch* b, const BSide& B, int dv, float omega, cudaStream_t s) {
+  const float keep = 1.0f - omega;
+  int64_t first = 0;
+  for (int c = 0; c < 3; ++c) {
+    const int G = class_lanes(b, c, dv);
+    const int VPL = next_pow2((dv + G - 1) / G);
+    if (B.weighted)
+      HNV_CHECK((launch_batched_dispatch<T, true>(G, VPL, B, first, B.n_cls[c], dv, keep, omega, s)));
+    else
+      HNV_CHECK((launch_batched_dispatch<T, false>(G, VPL, B, first, B.n_cls[c], dv, keep, omega, s)));
+    first += B.n_cls[c];
+  }
+  if (B.n_mid + B.n_huge > 0) {
+    constexpr int N = dev::VecT<T>::N;
+    const int32_t mid_blocks = (B.n_mid + kFinThreads / 32 - 1) / (kFinThreads / 32);
+    const size_t smem = sizeof(float) * (size_t)(kFinThreads / dv) * dv * N;
+    BTRACE("launch finalize mid=%d huge=%d smem=%zu", B.n_mid, B.n_huge, smem);
+    HNV_CHECK(launch("batched_finalize", batched_finalize_kernel<T>,
+                     (unsigned)(mid_blocks + B.n_huge), kFinThreads, smem, s,
+                     (const int4*)B.long_desc, (const int32_t*)B.long_g, B.n_mid, B.n_huge,
+                     mid_blocks, (const GraphSide*)B.sides, B.n_graphs, dv, keep, omega));
+  }
+  return HNV_OK;
+}
+
+template <typename T>
+int enqueue_vcycle(const hnv_batch* b, int d, float omega, int sweeps, cudaStream_t s) {
+  const int dv = (int)(d * sizeof(T) / 16);
+  for (int st = b->Lmax; st >= 0; --st) {
+    const BStep& S = b->steps[st];
+    BTRACE("enqueue step %d copies %d proj %d", st, S.n_copies, S.n_proj);
+    if (S.n_copies) {
+      BTRACE("launch copy step %d n=%d total=%lld", st, S.n_copies, (long long)S.copy_total);
+      HNV_CHECK(launch("batched_copy", batched_copy_kernel, (unsigned)(num_sms() * 8), 256, 0, s,
+                       (const CopyDesc*)S.copies, (const int64_t*)S.copy_prefix, S.n_copies,
+                       S.copy_total));
+    }
+    if (S.n_proj) {
+      BTRACE("launch project step %d n=%d total=%lld", st, S.n_proj, (long long)S.proj_total);
+      HNV_CHECK(launch("batched_project", batched_project_kernel, (unsigned)(num_sms() * 8), 256, 0,
+                       s, (const ProjDesc*)S.proj, (const int64_t*)S.proj_prefix, S.n_proj,
+                       S.proj_total, dv));
+    }
+    for (int it = 0; it < sweeps; ++it) {
+      HNV_CHECK(enqueue_half<T>(b, S.side[0], dv, omega, s));
+      HNV_CHECK(enqueue_half<T>(b, S.side[1], dv, omega, s));
+    }
+  }
+  return HNV_OK;
+}
+
+int enqueue(const hnv_batch* b, int dt, int d, float omega, int sweeps, cudaStream_t s) {
+  return dt == HNV_BF16 ? enqueue_vcycle<__nv_bfloat16>(b, d, omega, sweeps, s)
+                        : enqueue_vcycle<float>(b, d, omega, sweeps, s);
+}
+
+template <typename T>
+int enqueue_step0_sweep(const hnv_batch* b, int d, float omega, cudaStream_t s) {
+  const int dv = (int)(d * sizeof(T) / 16);
+  HNV_CHECK(enqueue_half<T>(b, b->steps[0].side[0], dv, omega, s));
+  return enqueue_half<T>(b, b->steps[0].side[1], dv, omega, s);
+}
+
+// milliseconds of one level-0 sweep over the batch (median of reps)
+int time_step0(const hnv_batch* b, int dt, int d, float omega, cudaStream_t s, float* ms) {
+  cudaEvent_t e0, e1;
+  HNV_CUDA(cudaEventCreate(&e0));
+  HNV_CUDA(cudaEventCreate(&e1));
+  std::vector<float> t;
+  int rc = HNV_OK;
+  for (int r = 0; r < 5 && rc == HNV_OK; ++r) {
+    cudaEventRecord(e0, s);
+    rc = dt == HNV_BF16 ? enqueue_step0_sweep<__nv_bfloat16>(b, d, omega, s)
+                        : enqueue_step0_sweep<float>(b, d, omega, s);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float x = 0.f;
+    cudaEventElapsedTime(&x, e0, e1);
+    if (r > 0) t.push_back(x);    // the first run warms the caches
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  HNV_CHECK(rc);
+  std::sort(t.begin(), t.end());
+  *ms = t[t.size() / 2];
+  return HNV_OK;
+}
+
+std::vector<int64_t> tune_key(const hnv_batch* b, int dt, int d) {
+  std::vector<int64_t> k{dt, d, (int64_t)b->graphs.size()};
+  int64_t hist[2][24] = {{0}};
+  for (hnv_graph* g : b->graphs) {
+    const Level& lv = g->levels[0];
+    std::vector<int32_t> e(lv.m + 1), v(lv.n + 1);
+    cudaMemcpy(e.data(), lv.e_ptr, sizeof(int32_t) * (lv.m + 1), cudaMemcpyDeviceToHost);
+    cudaMemcpy(v.data(), lv.v_ptr, sizeof(int32_t) * (lv.n + 1), cudaMemcpyDeviceToHost);
+    for (int side = 0; side < 2; ++side) {
+      const std::vector<int32_t>& p = side == 0 ? e : v;
+      for (size_t r = 0; r + 1 < p.size(); ++r) {
+        int len = p[r + 1] - p[r], bkt = 0;
+        while (bkt < 23 && (1 << bkt) < len) ++bkt;
+        ++hist[side][bkt];
+      }
+    }
+  }
+  // coarse signature: the share of rows per length bucket, in percent
+  for (int side = 0; side < 2; ++side) {
+    int64_t tot = 0;
+    for (int64_t x : hist[side]) tot += x;
+    for (int64_t x : hist[side]) k.push_back(tot ? (100 * x) / tot : 0);
+  }
+  return k;
+}
+
+}  // namespace
+}  // namespace hnv
+
+extern "C" {
+
+int hnv_batch_create(hnv_graph* const* graphs, int32_t count, hnv_batch** out) {
+  clear_error_detail();
+  if (!out) HNV_FAIL(HNV_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!graphs || count < 1) HNV_FAIL(HNV_ERR_INVALID_ARG, "need at least one graph");
+  int dev0 = -1;
+  for (int32_t i = 0; i < count; ++i) {
+    if (!graphs[i]) HNV_FAIL(HNV_ERR_INVALID_ARG, "graph %d is NULL", i);
+    if (dev0 < 0) dev0 = graphs[i]->device;
+    if (graphs[i]->device != dev0) HNV_FAIL(HNV_ERR_INVALID_ARG, "graphs on different devices");
+  }
+  // the graphs' arrays are read on the batch's own stream from here on
+  for (int32_t i = 0; i < count; ++i) {
+    const cudaError_t e = cudaStreamSynchronize(graphs[i]->stream);
+    if (e != cudaSuccess) return cuda_status(e, "cudaStreamSynchronize");
+  }
+  BTRACE("create: %d graphs synchronised", count);
+  hnv_batch* b = new (std::nothrow) hnv_batch();
+  if (!b) HNV_FAIL(HNV_ERR_OOM, "host allocation failed");
+  b->graphs.assign(graphs, graphs + count);
+  b->device = dev0;
+  b->coarse_off.assign(count + 1, 0);
+  b->v_off.assign(count + 1, 0);
+  b->e_off.assign(count + 1, 0);
+  for (int32_t i = 0; i < count; ++i) {
+    const hnv_graph* g = graphs[i];
+    const int L = (int)g->levels.size() - 1;
+    b->top.push_back(L);
+    b->Lmax = std::max(b->Lmax, L);
+    b->coarse_off[i + 1] = b->coarse_off[i] + g->levels[L].n + g->levels[L].m;
+    b->v_off[i + 1] = b->v_off[i] + g->levels[0].n;
+    b->e_off[i + 1] = b->e_off[i] + g->levels[0].m;
+  }
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(dev0);
+  cudaError_t e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+  if (prev >= 0) cudaSetDevice(prev);
+  if (e != cudaSuccess) {
+    delete b;
+    return cuda_status(e, "cudaStreamCreate");
+  }
+  *out = b;
+  return HNV_OK;
+}
+
+int hnv_batch_offsets(const hnv_batch* b, int64_t* coarsest_rows, int64_t* node_rows,
+                      int64_t* edge_rows) {
+  if (!b) HNV_FAIL(HNV_ERR_INVALID_ARG, "batch is NULL");
+  const size_t n = b->coarse_off.size();
+  if (coarsest_rows) std::memcpy(coarsest_rows, b->coarse_off.data(), n * sizeof(int64_t));
+  if (node_rows) std::memcpy(node_rows, b->v_off.data(), n * sizeof(int64_t));
+  if (edge_rows) std::memcpy(edge_rows, b->e_off.data(), n * sizeof(int64_t));
+  return HNV_OK;
+}
+
+int hnv_batch_autotune(hnv_batch* b, hnv_dtype dt, int d, float omega, hnv_batch_tuning* chosen) {
+  clear_error_detail();
+  if (!b) HNV_FAIL(HNV_ERR_INVALID_ARG, "batch is NULL");
+  if (dt != HNV_F32 && dt != HNV_BF16) HNV_FAIL(HNV_ERR_INVALID_ARG, "unknown dtype");
+  if (d < 8 || d > 1024 || d % 8) HNV_FAIL(HNV_ERR_UNSUPPORTED_D, "d must be a multiple of 8 in [8, 1024]");
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(b->device);
+  cudaStream_t s = b->cap_stream;
+  int rc = HNV_OK;
+  const std::vector<int64_t> key = tune_key(b, dt, d);
+  PlanShape best_shape = b->shape;
+  std::vector<int> best_lanes(3, 0);
+  float best_ms = -1.f;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      best_shape = it->second.first;
+      best_lanes = it->second.second;
+    }
+  }
+  const bool cached = best_lanes[0] != 0;
+  const size_t rb = (dt == HNV_BF16 ? 2 : 4) * (size_t)d;
+  const int dv = (int)(rb / 16);
+  uint8_t* zbuf = nullptr;
+  if (!cached) {
+    // scratch rows for level 0 of every graph (contents do not affect timing)
+    const size_t rows = (size_t)b->v_off.back() + b->e_off.back();
+    rc = dev_alloc((void**)&zbuf, rows * rb, s);
+    if (rc == HNV_OK) {
+      const cudaError_t e = cudaMemsetAsync(zbuf, 0, rows * rb, s);
+      if (e != cudaSuccess) rc = cuda_status(e, "cudaMemsetAsync");
+    }
+    const PlanShape shapes[3] = {{4, 16, 64}, {2, 8, 32}, {8, 32, 64}};
+    for (int si = 0; si < 3 && rc == HNV_OK; ++si) {
+      b->shape = shapes[si];
+      std::fill(b->lanes, b->lanes + 3, 0);
+      rc = build_plans(b, rb, s, 0);
+      if (rc == HNV_OK)
+        rc = build_steps(b, dt, d, zbuf, zbuf, zbuf + (size_t)b->v_off.back() * rb, s, 0);
+      // lanes per row of the two short classes
+      const int cand_a[3] = {2, 4, 8}, cand_b[3] = {4, 8, 16};
+      for (int ia = 0; ia < 3 && rc == HNV_OK; ++ia)
+        for (int ib = 0; ib < 3 && rc == HNV_OK; ++ib) {
+          b->lanes[0] = cand_a[ia];
+          b->lanes[1] = cand_b[ib];
+          b->lanes[2] = 0;
+          if (class_lanes(b, 0, dv) != cand_a[ia] || class_lanes(b, 1, dv) != cand_b[ib]) continue;
+          float ms = 0.f;
+          rc = time_step0(b, dt, d, omega, s, &ms);
+          if (rc == HNV_OK && (best_ms < 0.f || ms < best_ms)) {
+            best_ms = ms;
+            best_shape = shapes[si];
+            best_lanes = {cand_a[ia], cand_b[ib], 0};
+          }
+        }
+    }
+    if (zbuf) dev_free(zbuf, s);
+    if (rc == HNV_OK) {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tune_cache[key] = {best_shape, best_lanes};
+    }
+  }
+  if (rc == HNV_OK) {
+    b->shape = best_shape;
+    for (int c = 0; c < 3; ++c) b->lanes[c] = best_lanes[c];
+    free_steps(b, s);
+    b->plans_ready = false;
+    if (chosen) {
+      chosen->a_max = best_shape.a_max;
+      chosen->b_max = best_shape.b_max;
+      chosen->c_max = best_shape.c_max;
+      chosen->lanes_a = class_lanes(b, 0, dv);
+      chosen->lanes_b = class_lanes(b, 1, dv);
+      chosen->lanes_rest = class_lanes(b, 2, dv);
+      chosen->best_ms = best_ms;
+      chosen->from_cache = cached ? 1 : 0;
+    }
+  }
+  cudaStreamSynchronize(s);
+  if (prev >= 0) cudaSetDevice(prev);
+  return rc;
+}
+
+int hnv_batch_vcycle(hnv_batch* b, const void* z_coarsest, void* z_v_out, void* z_e_out,
+                     hnv_dtype dt, int d, float omega, int sweeps_per_level, int use_cuda_graph,
+                     hnv_stream_t stream) {
+  clear_error_detail();
+  if (!b) HNV_FAIL(HNV_ERR_INVALID_ARG, "batch is NULL");
+  if (dt != HNV_F32 && dt != HNV_BF16) HNV_FAIL(HNV_ERR_INVALID_ARG, "unknown dtype");
+  if (d < 8 || d > 1024 || d % 8)
+    HNV_FAIL(HNV_ERR_UNSUPPORTED_D, "batched d must be a multiple of 8 in [8, 1024]");
+  if (!(omega >= 0.f && omega <= 1.f)) HNV_FAIL(HNV_ERR_INVALID_ARG, "omega must be in [0, 1]");
+  if (sweeps_per_level < 0) HNV_FAIL(HNV_ERR_INVALID_ARG, "sweeps_per_level < 0");
+  if (!z_coarsest || !z_v_out || !z_e_out) HNV_FAIL(HNV_ERR_INVALID_ARG, "NULL buffer");
+  if ((reinterpret_cast<uintptr_t>(z_coarsest) | reinterpret_cast<uintptr_t>(z_v_out) |
+       reinterpret_cast<uintptr_t>(z_e_out)) & 15u)
+    HNV_FAIL(HNV_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(b->device);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaStream_t cs = b->cap_stream;
+  int rc = HNV_OK;
+  do {
+    const size_t rb = (dt == HNV_BF16 ? 2 : 4) * (size_t)d;
+    if (!b->plans_ready || b->plans_row_bytes != rb) {
+      if ((rc = build_plans(b, rb, cs)) != HNV_OK) break;
+      free_steps(b, cs);
+    }
+    if (b->built_dt != (int)dt || b->built_d != d || b->built_zc != z_coarsest ||
+        b->built_zv != z_v_out || b->built_ze != z_e_out || b->steps.empty()) {
+      if ((rc = build_steps(b, dt, d, (const uint8_t*)z_coarsest, (uint8_t*)z_v_out,
+                            (uint8_t*)z_e_out, cs)) != HNV_OK)
+        break;
+      b->built_zc = z_coarsest;
+      b->built_zv = z_v_out;
+      b->built_ze = z_e_out;
+    }
+    // the caller's stream must see the set-up work done on the batch stream
+    {
+      const cudaError_t e = cudaStreamSynchronize(cs);
+      if (e != cudaSuccess) {
+        rc = cuda_status(e, "cudaStreamSynchronize");
+        break;
+      }
+    }
+    if (!use_cuda_graph) {
+      rc = enqueue(b, (int)dt, d, omega, sweeps_per_level, s);
+      BTRACE("direct enqueue rc=%d", rc);
+      break;
+    }
+    if (!b->exec || b->exec_omega != omega || b->exec_sweeps != sweeps_per_level) {
+      if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+      }
+      cudaGraph_t graph = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) { rc = cuda_status(e, "cudaStreamBeginCapture"); break; }
+      const int64_t before = hnv_kernel_launch_count();
+      const int erc = enqueue(b, (int)dt, d, omega, sweeps_per_level, cs);
+      // captured launches run at replay: count them there, not here
+      b->exec_kernels = hnv_kernel_launch_count() - before;
+      note_launches(-b->exec_kernels);
+      e = cudaStreamEndCapture(cs, &graph);
+      if (erc != HNV_OK) { if (graph) cudaGraphDestroy(graph); rc = erc; break; }
+      if (e != cudaSuccess) { rc = cuda_status(e, "cudaStreamEndCapture"); break; }
+      e = cudaGraphInstantiate(&b->exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) { b->exec = nullptr; rc = cuda_status(e, "cudaGraphInstantiate"); break; }
+      b->exec_omega = omega;
+      b->exec_sweeps = sweeps_per_level;
+    }
+    BTRACE("graph launch (%lld kernels)", (long long)b->exec_kernels);
+    cudaError_t e = cudaGraphLaunch(b->exec, s);
+    if (e != cudaSuccess) rc = cuda_status(e, "cudaGraphLaunch");
+    else note_launches(b->exec_kernels);
+  } while (0);
+  if (prev >= 0) cudaSetDevice(prev);
+  return rc;
+}
+
+void hnv_batch_free(hnv_batch* b) {
+  if (!b) return;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(b->device);
+  free_steps(b, b->cap_stream);
+  free_list(b->plan_owned, b->cap_stream);
+  cudaStreamSynchronize(b->cap_stream);
+  cudaStreamDestroy(b->cap_stream);
+  if (prev >= 0) cudaSetDevice(prev);
+  delete b;
+}
+
+}  // extern "C"

@@ -44,35 +44,80 @@ __global__ void priority_kernel(int32_t m, int32_t policy, uint64_t salt,
 }
 
 // c(v) = argmin_{e in N(v)} (prio(e), e), or -1; warp per node, lanes stride
-// the CSC row, then a lexicographic min over the warp.
+// the CSC row, then a lexicographic min over the warp. Rows longer than
+// kLongRow go to `long_rows` for assign_long_kernel (block per row).
+constexpr int32_t kLongRow = 4096;
+constexpr int kLongThreads = 512;
+
+__device__ __forceinline__ void lex_min(uint64_t& bp, int32_t& be, uint64_t p, int32_t e) {
+  if (p < bp || (p == bp && e < be)) {
+    bp = p;
+    be = e;
+  }
+}
+
 __global__ void assign_kernel(int32_t n, const int32_t* __restrict__ v_ptr,
                               const int32_t* __restrict__ v_edges,
-                              const uint64_t* __restrict__ prio, int32_t* __restrict__ c) {
+                              const uint64_t* __restrict__ prio, int32_t* __restrict__ c,
+                              int32_t* __restrict__ long_rows, int32_t* __restrict__ n_long) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t v = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); v < n;
        v += warps) {
     const int64_t b = v_ptr[v], end = v_ptr[v + 1];
+    if (end - b > kLongRow) {
+      if (lane == 0) long_rows[atomicAdd(n_long, 1)] = (int32_t)v;
+      continue;
+    }
     uint64_t bp = ~0ull;
     int32_t be = 0x7fffffff;
     for (int64_t k = b + lane; k < end; k += 32) {
       const int32_t e = v_edges[k];
-      const uint64_t p = prio[e];
-      if (p < bp || (p == bp && e < be)) {
-        bp = p;
-        be = e;
-      }
+      lex_min(bp, be, prio[e], e);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const uint64_t op = __shfl_xor_sync(FULL, bp, o);
       const int32_t oe = __shfl_xor_sync(FULL, be, o);
-      if (op < bp || (op == bp && oe < be)) {
-        bp = op;
-        be = oe;
-      }
+      lex_min(bp, be, op, oe);
     }
     if (lane == 0) c[v] = (end > b) ? be : -1;
+  }
+}
+
+__global__ void __launch_bounds__(kLongThreads)
+assign_long_kernel(const int32_t* __restrict__ long_rows, const int32_t* __restrict__ n_long,
+                   const int32_t* __restrict__ v_ptr, const int32_t* __restrict__ v_edges,
+                   const uint64_t* __restrict__ prio, int32_t* __restrict__ c) {
+  __shared__ uint64_t sp[kLongThreads / 32];
+  __shared__ int32_t se[kLongThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int32_t count = *n_long;
+  for (int32_t i = blockIdx.x; i < count; i += gridDim.x) {
+    const int32_t v = long_rows[i];
+    const int64_t b = v_ptr[v], end = v_ptr[v + 1];
+    uint64_t bp = ~0ull;
+    int32_t be = 0x7fffffff;
+    for (int64_t k = b + threadIdx.x; k < end; k += kLongThreads) {
+      const int32_t e = v_edges[k];
+      lex_min(bp, be, prio[e], e);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const uint64_t op = __shfl_xor_sync(FULL, bp, o);
+      const int32_t oe = __shfl_xor_sync(FULL, be, o);
+      lex_min(bp, be, op, oe);
+    }
+    if (lane == 0) {
+      sp[w] = bp;
+      se[w] = be;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int q = 1; q < kLongThreads / 32; ++q) lex_min(bp, be, sp[q], se[q]);
+      c[v] = be;
+    }
+    __syncthreads();
   }
 }
 
@@ -107,6 +152,81 @@ __global__ void pack_image_keys(int32_t m, const int32_t* __restrict__ e_ptr,
     for (int64_t k = b + lane; k < end; k += 32)
       keys[k] = ((uint64_t)(uint32_t)e << 32) | (uint32_t)rep_v[e_nodes[k]];
   }
+}
+
+// Segmented sort of the image keys: the keys were packed hyperedge by
+// hyperedge, so sorting every hyperedge's segment [e_ptr[e], e_ptr[e+1]) by
+// its low word gives the array a full sort by (e, rep) would. Segments of
+// at most 32 keys: a warp each, bitonic network over the lanes. Up to
+// kSegMax: a block each, bitonic network in shared memory. Longer segments
+// exist only if the level has hyperedges that long; the caller then sorts
+// the whole array instead.
+constexpr int32_t kSegMax = 4096;
+constexpr int kSegThreads = 512;
+
+__global__ void seg_sort_warp(int32_t m, const int32_t* __restrict__ e_ptr,
+                              uint64_t* __restrict__ keys) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); e < m;
+       e += warps) {
+    const int32_t b = e_ptr[e], len = e_ptr[e + 1] - b;
+    if (len < 2 || len > 32) continue;
+    uint32_t x = lane < len ? (uint32_t)keys[b + lane] : 0xffffffffu;
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        const uint32_t o = __shfl_xor_sync(FULL, x, j);
+        const bool ascending = (lane & k) == 0;
+        const bool lower = (lane & j) == 0;
+        x = (lower == ascending) ? min(x, o) : max(x, o);
+      }
+    }
+    if (lane < len) keys[b + lane] = ((uint64_t)(uint32_t)e << 32) | x;
+  }
+}
+
+__global__ void __launch_bounds__(kSegThreads)
+seg_sort_block(int32_t m, const int32_t* __restrict__ e_ptr, uint64_t* __restrict__ keys) {
+  __shared__ uint32_t sk[kSegMax];
+  for (int64_t e = blockIdx.x; e < m; e += gridDim.x) {
+    const int32_t b = e_ptr[e], len = e_ptr[e + 1] - b;
+    if (len <= 32 || len > kSegMax) continue;
+    int32_t n2 = 64;
+    while (n2 < len) n2 <<= 1;
+    for (int32_t i = threadIdx.x; i < n2; i += kSegThreads)
+      sk[i] = i < len ? (uint32_t)keys[b + i] : 0xffffffffu;
+    __syncthreads();
+    for (int32_t k = 2; k <= n2; k <<= 1) {
+      for (int32_t j = k >> 1; j > 0; j >>= 1) {
+        for (int32_t i = threadIdx.x; i < n2; i += kSegThreads) {
+          const int32_t p = i ^ j;
+          if (p > i) {
+            const uint32_t a = sk[i], c = sk[p];
+            const bool ascending = (i & k) == 0;
+            if ((a > c) == ascending) {
+              sk[i] = c;
+              sk[p] = a;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (int32_t i = threadIdx.x; i < len; i += kSegThreads)
+      keys[b + i] = ((uint64_t)(uint32_t)e << 32) | sk[i];
+    __syncthreads();
+  }
+}
+
+__global__ void max_row_len(int32_t rows, const int32_t* __restrict__ ptr, int32_t* __restrict__ out) {
+  int32_t mx = 0;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows;
+       r += (int64_t)gridDim.x * blockDim.x)
+    mx = max(mx, ptr[r + 1] - ptr[r]);
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(FULL, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx) atomicMax(out, mx);
 }
 
 __global__ void image_first_kernel(const uint64_t* __restrict__ keys, int64_t n,
@@ -187,7 +307,15 @@ int coarsen_step(hnv_graph* g, int level, const hnv_coarsen_params* p,
   HNV_CHECK(launch("priority", priority_kernel, grid_for(m, 256), 256, 0, s, m, p->policy, salt,
                    (const int32_t*)fine->e_ptr, (const float*)fine->w,
                    (const int32_t*)fine->orig_e, d_explicit, prio));
+  int32_t *long_rows = nullptr, *n_long = nullptr;
+  HNV_CHECK(pool.get(&long_rows, (size_t)(nnz / kLongRow + 1)));
+  HNV_CHECK(pool.get(&n_long, 1));
+  HNV_CUDA(cudaMemsetAsync(n_long, 0, sizeof(int32_t), s));
   HNV_CHECK(launch("assign", assign_kernel, grid_for((int64_t)n * 32, 256), 256, 0, s, n,
+                   (const int32_t*)fine->v_ptr, (const int32_t*)fine->v_edges,
+                   (const uint64_t*)prio, c, long_rows, n_long));
+  HNV_CHECK(launch("assign_long", assign_long_kernel, (unsigned)(2 * num_sms()), kLongThreads, 0,
+                   s, (const int32_t*)long_rows, (const int32_t*)n_long,
                    (const int32_t*)fine->v_ptr, (const int32_t*)fine->v_edges,
                    (const uint64_t*)prio, c));
 
@@ -199,8 +327,12 @@ int coarsen_step(hnv_graph* g, int level, const hnv_coarsen_params* p,
   HNV_CHECK(launch("mark_keys", mark_keys_kernel, grid_for(n, 256), 256, 0, s, n, m,
                    (const int32_t*)c, rank));
   HNV_CHECK(exclusive_scan_i32(rank, rank, nkeys, g->d_buf, s));
-  int32_t n2 = 0;
-  HNV_CHECK(read_ints(g, g->d_buf, 1, &n2, s));
+  HNV_CUDA(cudaMemsetAsync(g->d_buf + 1, 0, sizeof(int32_t), s));
+  HNV_CHECK(launch("max_row_len", max_row_len, grid_for(m, 256), 256, 0, s, m,
+                   (const int32_t*)fine->e_ptr, g->d_buf + 1));
+  int32_t nm[2];
+  HNV_CHECK(read_ints(g, g->d_buf, 2, nm, s));
+  const int32_t n2 = nm[0], max_e_len = nm[1];
   HNV_CHECK(level_alloc(fine, (void**)&fine->rep_v, sizeof(int32_t) * (size_t)n, s));
   HNV_CHECK(level_alloc(fine, (void**)&fine->rep_e, sizeof(int32_t) * (size_t)m, s));
   HNV_CHECK(launch("rep_v", rep_v_kernel, grid_for(n, 256), 256, 0, s, n, m, (const int32_t*)c,
@@ -214,9 +346,18 @@ int coarsen_step(hnv_graph* g, int level, const hnv_coarsen_params* p,
   HNV_CHECK(launch("pack_image_keys", pack_image_keys, grid_for((int64_t)m * 32, 256), 256, 0, s,
                    m, (const int32_t*)fine->e_ptr, (const int32_t*)fine->e_nodes,
                    (const int32_t*)fine->rep_v, k0));
-  int shifts[16];
-  const int np = radix_shifts(bits_for_count(n2), bits_for_count(m), shifts);
-  HNV_CHECK(radix_sort_u64(k0, k1, nnz, shifts, np, s, &sorted));
+  if (max_e_len <= kSegMax) {
+    HNV_CHECK(launch("seg_sort_warp", seg_sort_warp, grid_for((int64_t)m * 32, 256), 256, 0, s, m,
+                     (const int32_t*)fine->e_ptr, k0));
+    if (max_e_len > 32)
+      HNV_CHECK(launch("seg_sort_block", seg_sort_block, (unsigned)(4 * num_sms()), kSegThreads, 0,
+                       s, m, (const int32_t*)fine->e_ptr, k0));
+    sorted = k0;
+  } else {
+    int shifts[16];
+    const int np = radix_shifts(bits_for_count(n2), bits_for_count(m), shifts);
+    HNV_CHECK(radix_sort_u64(k0, k1, nnz, shifts, np, s, &sorted));
+  }
   HNV_CHECK(pool.get(&first, (size_t)nnz));
   HNV_CHECK(pool.get(&img_size, (size_t)m + 1));
   HNV_CHECK(pool.get(&keep, (size_t)m + 1));

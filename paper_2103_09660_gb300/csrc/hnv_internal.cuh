@@ -46,7 +46,8 @@ enum : int32_t {
   ERRBIT_EMPTY_EDGE = 2,    // an input hyperedge with no members
   ERRBIT_BAD_WEIGHT = 4,    // a weight that is not finite and > 0
   ERRBIT_BAD_PTR = 8,       // edge_ptr not starting at 0 / decreasing
-  ERRBIT_TIMEOUT = 16       // a bounded device wait gave up (refinement)
+  ERRBIT_TIMEOUT = 16,      // a bounded device wait gave up (refinement)
+  ERRBIT_BAD_ITEM = 32      // a batched work item outside its graph's arrays (skipped)
 };
 
 // ---------------------------------------------------------------------------
@@ -54,6 +55,7 @@ enum : int32_t {
 // ---------------------------------------------------------------------------
 
 void note_launch();
+void note_launches(int64_t k);   // k kernels at once (a replayed CUDA graph)
 int num_sms();
 
 // Launches kernel<<<grid, block, smem, s>>>(args...) and counts it. A launch
@@ -168,6 +170,15 @@ int transpose_csr(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t* ro
 constexpr int32_t kSplitT = 128;
 constexpr int32_t kMidChunks = 32;
 
+// Class boundaries of a plan (lengths: A <= a_max < B <= b_max < C <= c_max
+// < D <= T). The single-graph path uses the defaults; the batched path takes
+// them from its autotuner.
+struct PlanShape {
+  int32_t a_max = 4;
+  int32_t b_max = 16;
+  int32_t c_max = 64;
+};
+
 struct SplitPlan {
   int32_t T = kSplitT;
   int32_t n_a = 0, n_b = 0, n_c = 0, n_d = 0;  // rows per class
@@ -203,6 +214,13 @@ struct Level {
   int32_t* ch_idx = nullptr;     //   fine nodes v, then collapsed hyperedges n + e
   SplitPlan planC;
   std::vector<void*> owned;      // every device allocation of this level
+  // panel plans of the two sides (0 hyperedge rows, 1 node rows) for the
+  // row size they were chosen for (side_plan); kept apart from `owned` so
+  // that they can be rebuilt for another row size
+  SplitPlan panel_plan[2];
+  int32_t panel_P[2] = {1, 1};
+  size_t panel_rb[2] = {0, 0};
+  std::vector<void*> panel_owned[2];
 };
 
 }  // namespace hnv
@@ -228,9 +246,29 @@ int build_level0(hnv_graph* g, int32_t n, int32_t m, const int64_t* d_edge_ptr,
 int finish_level(hnv_graph* g, Level* lv);   // derived arrays + plans
 // Weight-dependent arrays of a level (v_w, deg_v, inv_deg_v) from lv->w.
 int level_weight_arrays(Level* lv, cudaStream_t s);
-// Split-row work plan of a CSR with `rows` rows (allocations owned by lv).
-int build_split_plan(hnv_graph* g, Level* lv, const int32_t* ptr, int32_t rows, SplitPlan* plan,
-                     cudaStream_t s);
+// Split-row work plan of a CSR with `rows` rows; its device allocations are
+// appended to `owned` (freed by whoever owns that list).
+int build_split_plan(hnv_graph* g, std::vector<void*>* owned, const int32_t* ptr, int32_t rows,
+                     SplitPlan* plan, cudaStream_t s, const PlanShape& shape = PlanShape());
+// Panel plan: the rows of `base` no longer than its class C bound keep their
+// classes and items; the longer rows (listed ascending neighbour IDs in
+// [0, cols)) are cut where their neighbours cross a panel boundary (P equal
+// ranges of IDs) and into chunks of at most T incidences, and their items
+// are listed panel by panel after the short classes, so that the launch
+// over them works through the neighbour table one panel at a time (a
+// panel's rows are read from DRAM about once and then hit L2). A long row
+// left in one piece is a row item (n_d counts them); the pieces of a cut
+// row are reduced in order (panel, then position) by the split-row
+// reduction. P is chosen from table_bytes (the neighbour table's size) and
+// the long rows' lengths; *panels = 1 means no panel plan (plan untouched).
+int build_panel_plan(hnv_graph* g, std::vector<void*>* owned, const SplitPlan& base,
+                     const int32_t* ptr, const int32_t* idx, int32_t cols, int64_t table_bytes,
+                     SplitPlan* plan, int* panels, cudaStream_t s);
+// The plan of one side of a level (0 hyperedge rows, 1 node rows) for
+// neighbour rows of row_bytes: its panel plan (built on first use) or the
+// regular one. HNV_PANELS=<k> forces k panels wherever there are long rows.
+int side_plan(hnv_graph* g, Level* lv, int side, size_t row_bytes, const SplitPlan** plan,
+              cudaStream_t s);
 void free_level(Level* lv, cudaStream_t s);
 int level_alloc(Level* lv, void** p, size_t bytes, cudaStream_t s);
 

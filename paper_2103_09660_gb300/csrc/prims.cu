@@ -184,10 +184,18 @@ __global__ void pack_col_row(int32_t n_rows, const int32_t* __restrict__ row_ptr
   }
 }
 
-__global__ void count_high(const uint64_t* __restrict__ keys, int64_t n, int32_t* __restrict__ cnt) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    atomicAdd(&cnt[(uint32_t)(keys[i] >> 32)], 1);
+// col_ptr of keys sorted by their high word (the column): position i starts
+// every column in (col(i-1), col(i)], with col(-1) = -1 and col(n) = n_cols,
+// so col_ptr[c] = first position whose column is >= c. No atomics: each
+// entry of col_ptr[0..n_cols] is written by exactly one position.
+__global__ void col_starts(const uint64_t* __restrict__ keys, int64_t n, int32_t n_cols,
+                           int32_t* __restrict__ col_ptr) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t prev = i > 0 ? (int64_t)(uint32_t)(keys[i - 1] >> 32) : -1;
+    const int64_t cur = i < n ? (int64_t)(uint32_t)(keys[i] >> 32) : (int64_t)n_cols;
+    for (int64_t c = prev + 1; c <= cur; ++c) col_ptr[c] = (int32_t)i;
+  }
 }
 
 __global__ void low_words(const uint64_t* __restrict__ keys, int64_t n, int32_t* __restrict__ out) {
@@ -264,25 +272,23 @@ int fill_i32(int32_t* p, int32_t value, int64_t n, cudaStream_t s) {
 
 int transpose_csr(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t* row_ptr,
                   const int32_t* cols, int32_t* col_ptr, int32_t* col_rows, cudaStream_t s) {
-  TempPool pool(s);
-  int32_t* cnt = nullptr;
-  HNV_CHECK(pool.get(&cnt, (size_t)n_cols + 1));
-  HNV_CUDA(cudaMemsetAsync(cnt, 0, ((size_t)n_cols + 1) * sizeof(int32_t), s));
-  if (nnz > 0) {
-    uint64_t *k0 = nullptr, *k1 = nullptr, *sorted = nullptr;
-    HNV_CHECK(pool.get(&k0, (size_t)nnz));
-    HNV_CHECK(pool.get(&k1, (size_t)nnz));
-    HNV_CHECK(launch("pack_col_row", pack_col_row, grid_for((int64_t)n_rows * 32, 256), 256, 0, s,
-                     n_rows, row_ptr, cols, k0));
-    int shifts[16];
-    int np = radix_shifts(0, bits_for_count(n_cols), shifts);
-    HNV_CHECK(radix_sort_u64(k0, k1, nnz, shifts, np, s, &sorted));
-    HNV_CHECK(launch("count_high", count_high, grid_for(nnz, 256), 256, 0, s,
-                     (const uint64_t*)sorted, nnz, cnt));
-    HNV_CHECK(launch("low_words", low_words, grid_for(nnz, 256), 256, 0, s,
-                     (const uint64_t*)sorted, nnz, col_rows));
+  if (nnz == 0) {
+    HNV_CUDA(cudaMemsetAsync(col_ptr, 0, ((size_t)n_cols + 1) * sizeof(int32_t), s));
+    return HNV_OK;
   }
-  return exclusive_scan_i32(cnt, col_ptr, (int64_t)n_cols + 1, nullptr, s);
+  TempPool pool(s);
+  uint64_t *k0 = nullptr, *k1 = nullptr, *sorted = nullptr;
+  HNV_CHECK(pool.get(&k0, (size_t)nnz));
+  HNV_CHECK(pool.get(&k1, (size_t)nnz));
+  HNV_CHECK(launch("pack_col_row", pack_col_row, grid_for((int64_t)n_rows * 32, 256), 256, 0, s,
+                   n_rows, row_ptr, cols, k0));
+  int shifts[16];
+  int np = radix_shifts(0, bits_for_count(n_cols), shifts);
+  HNV_CHECK(radix_sort_u64(k0, k1, nnz, shifts, np, s, &sorted));
+  HNV_CHECK(launch("col_starts", col_starts, grid_for(nnz + 1, 256), 256, 0, s,
+                   (const uint64_t*)sorted, nnz, n_cols, col_ptr));
+  return launch("low_words", low_words, grid_for(nnz, 256), 256, 0, s, (const uint64_t*)sorted,
+                nnz, col_rows);
 }
 
 }  // namespace hnv

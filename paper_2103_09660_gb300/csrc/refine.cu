@@ -24,56 +24,13 @@
 
 #include <cstdlib>
 
-#include "hnv_internal.cuh"
+#include "refine_device.cuh"
 
 namespace hnv {
 
 namespace {
 
-constexpr unsigned FULL = 0xffffffffu;
-
-// A row is a sequence of 16-byte vectors: 4 float32 or 8 bfloat16 values.
-// Arithmetic is float32 either way; VecT converts a vector to and from its
-// float values (bfloat16 to float is exact; float to bfloat16 rounds to
-// nearest even on store).
-template <typename T>
-struct VecT;
-
-template <>
-struct VecT<float> {
-  static constexpr int N = 4;
-  __device__ __forceinline__ static void unpack(const uint4& v, float* f) {
-    f[0] = __uint_as_float(v.x);
-    f[1] = __uint_as_float(v.y);
-    f[2] = __uint_as_float(v.z);
-    f[3] = __uint_as_float(v.w);
-  }
-  __device__ __forceinline__ static uint4 pack(const float* f) {
-    return make_uint4(__float_as_uint(f[0]), __float_as_uint(f[1]), __float_as_uint(f[2]),
-                      __float_as_uint(f[3]));
-  }
-};
-
-template <>
-struct VecT<__nv_bfloat16> {
-  static constexpr int N = 8;
-  // each 32-bit word holds two values, the lower-indexed one in the low half
-  __device__ __forceinline__ static void unpack(const uint4& v, float* f) {
-    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      f[2 * k] = __uint_as_float(w[k] << 16);
-      f[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
-    }
-  }
-  __device__ __forceinline__ static uint32_t pair(float lo, float hi) {
-    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<const uint32_t*>(&h);
-  }
-  __device__ __forceinline__ static uint4 pack(const float* f) {
-    return make_uint4(pair(f[0], f[1]), pair(f[2], f[3]), pair(f[4], f[5]), pair(f[6], f[7]));
-  }
-};
+using dev::VecT;
 
 template <typename T, int G, int VPL, bool WEIGHTED>
 __global__ void __launch_bounds__(256)
@@ -81,169 +38,26 @@ gather_kernel(const int4* __restrict__ items, int32_t n_items, const int32_t* __
               const float* __restrict__ inc_w, const float* __restrict__ inv_norm,
               const uint4* __restrict__ src, const uint4* self_in, uint4* out, int32_t dv,
               float keep, float scale, float* __restrict__ partials) {
-  using V = VecT<T>;
-  constexpr int N = V::N;
   constexpr int R = 32 / G;                                    // items per warp pass
-  // row loads in flight per lane (the weighted variant also holds a weight
-  // per load, so it takes half as many to keep its register count down)
-  constexpr int UB0 = (VPL == 1) ? 8 : (VPL == 2 ? 4 : (VPL == 4 ? 2 : 1));
-  constexpr int UB = (WEIGHTED && UB0 > 1) ? UB0 / 2 : UB0;
-  constexpr int U = UB < G ? UB : G;
   const int lane = threadIdx.x & 31;
   const int grp = lane / G;
   const int lg = lane & (G - 1);
   const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
-  const bool read_self = keep != 0.f;
-  const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
-
   for (int64_t wbase = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * R;
        wbase < n_items; wbase += warps_total * R) {
     const int64_t item = wbase + grp;
     int4 it = make_int4(-1, 0, 0, -1);
     if (item < n_items) it = __ldg(items + item);
-    const int32_t row = it.x, beg = it.y, len = it.z, slot = it.w;
-    const bool is_row = (row >= 0) && (slot < 0);
-
-    uint4 sv[VPL];
-#pragma unroll
-    for (int j = 0; j < VPL; ++j) sv[j] = zero4;
-    if (is_row && read_self) {
-#pragma unroll
-      for (int j = 0; j < VPL; ++j) {
-        const int col = lg + j * G;
-        if (col < dv) sv[j] = self_in[(size_t)row * dv + col];
-      }
-    }
-    float acc[VPL][N];
-#pragma unroll
-    for (int j = 0; j < VPL; ++j)
-#pragma unroll
-      for (int e = 0; e < N; ++e) acc[j][e] = 0.f;
-
-    const int32_t maxlen = __reduce_max_sync(FULL, len);
-    for (int32_t off = 0; off < maxlen; off += G) {
-      const int32_t mine = len - off;
-      const bool have = lg < mine;
-      const int32_t my_idx = have ? __ldg(idx + beg + off + lg) : 0;
-      float my_w = 0.f;
-      if (WEIGHTED) my_w = have ? __ldg(inc_w + beg + off + lg) : 0.f;
-      const int32_t cnt = min(G, maxlen - off);
-      for (int32_t t = 0; t < cnt; t += U) {
-        uint4 x[U][VPL];
-        float wt[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int sl = (t + u) & (G - 1);
-          const int32_t nb = __shfl_sync(FULL, my_idx, sl, G);
-          const bool ok = (t + u) < mine;
-          wt[u] = WEIGHTED ? (ok ? __shfl_sync(FULL, my_w, sl, G) : 0.f) : 1.f;
-          const uint4* rowp = src + (size_t)nb * dv;
-#pragma unroll
-          for (int j = 0; j < VPL; ++j) {
-            const int col = lg + j * G;
-            x[u][j] = (ok && col < dv) ? __ldg(rowp + col) : zero4;
-          }
-        }
-        // invalid slots loaded zeros (and weight 0): adding them is exact
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-#pragma unroll
-          for (int j = 0; j < VPL; ++j) {
-            float xf[N];
-            V::unpack(x[u][j], xf);
-#pragma unroll
-            for (int e = 0; e < N; ++e) {
-              if (WEIGHTED)
-                acc[j][e] = fmaf(wt[u], xf[e], acc[j][e]);
-              else
-                acc[j][e] += xf[e];
-            }
-          }
-        }
-      }
-    }
-
-    if (is_row) {
-      const float sc = inv_norm ? scale * inv_norm[row] : scale;
-#pragma unroll
-      for (int j = 0; j < VPL; ++j) {
-        const int col = lg + j * G;
-        if (col < dv) {
-          float sf[N], r[N];
-          V::unpack(sv[j], sf);
-#pragma unroll
-          for (int e = 0; e < N; ++e) r[e] = fmaf(keep, sf[e], sc * acc[j][e]);
-          out[(size_t)row * dv + col] = V::pack(r);
-        }
-      }
-    } else if (slot >= 0) {
-#pragma unroll
-      for (int j = 0; j < VPL; ++j) {
-        const int col = lg + j * G;
-        if (col < dv) {
-          float4* pp = reinterpret_cast<float4*>(partials + ((size_t)slot * dv + col) * N);
-#pragma unroll
-          for (int q = 0; q < N / 4; ++q)
-            pp[q] = make_float4(acc[j][4 * q], acc[j][4 * q + 1], acc[j][4 * q + 2],
-                                acc[j][4 * q + 3]);
-        }
-      }
-    }
+    dev::gather_item<T, G, VPL, WEIGHTED>(it, lg, idx, inc_w, inv_norm, src, self_in, out, dv,
+                                          keep, scale, partials);
   }
 }
 
-// Reduces the chunk partials of split rows in chunk order and relaxes
-// (out = keep * own row + scale * normaliser * sum, as gather_kernel).
-// Blocks [0, mid_blocks) give one warp to each of the first n_mid rows (at
-// most kMidChunks chunks: lanes over row vectors, four interleaved
-// accumulators); each later block takes one of the n_huge rows: S =
-// blockDim / dv slices sum contiguous runs of chunks (four interleaved
-// accumulators each) and slice 0 adds the slices in order.
+// Reduces the chunk partials of split rows. Blocks [0, mid_blocks) give one
+// warp to each of the first n_mid rows (at most kMidChunks chunks); each
+// later block takes one of the n_huge rows (slices of the block sum
+// contiguous runs of chunks, slice 0 adds the slices in order).
 constexpr int kFinThreads = 1024;
-
-__device__ __forceinline__ void f4_add(float4& a, const float4& b) {
-  a.x += b.x;
-  a.y += b.y;
-  a.z += b.z;
-  a.w += b.w;
-}
-
-// Sum of count float4 values p[0], p[stride], p[2*stride], ... (fixed order).
-__device__ __forceinline__ float4 sum_strided4(const float4* __restrict__ p, int32_t count,
-                                               int32_t stride) {
-  float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, a2 = a0, a3 = a0;
-  int32_t c = 0;
-  for (; c + 4 <= count; c += 4) {
-    const float4 p0 = p[(size_t)c * stride];
-    const float4 p1 = p[(size_t)(c + 1) * stride];
-    const float4 p2 = p[(size_t)(c + 2) * stride];
-    const float4 p3 = p[(size_t)(c + 3) * stride];
-    f4_add(a0, p0);
-    f4_add(a1, p1);
-    f4_add(a2, p2);
-    f4_add(a3, p3);
-  }
-  for (; c < count; ++c) f4_add(a0, p[(size_t)c * stride]);
-  f4_add(a0, a1);
-  f4_add(a2, a3);
-  f4_add(a0, a2);
-  return a0;
-}
-
-// Sum over `count` chunks of one row vector's N partial floats.
-template <int N>
-__device__ __forceinline__ void sum_chunks(const float* __restrict__ partials, int32_t first,
-                                           int32_t count, int32_t dv, int32_t col, float* out) {
-  const float4* base = reinterpret_cast<const float4*>(partials) + ((size_t)first * dv + col) * (N / 4);
-#pragma unroll
-  for (int q = 0; q < N / 4; ++q) {
-    const float4 t = sum_strided4(base + q, count, dv * (N / 4));
-    out[4 * q] = t.x;
-    out[4 * q + 1] = t.y;
-    out[4 * q + 2] = t.z;
-    out[4 * q + 3] = t.w;
-  }
-}
 
 template <typename T>
 __global__ void __launch_bounds__(kFinThreads)
@@ -251,58 +65,18 @@ finalize_kernel(const int4* __restrict__ long_desc, int32_t n_mid, int32_t n_hug
                 int32_t mid_blocks, const float* __restrict__ partials,
                 const float* __restrict__ inv_norm, const uint4* self_in, uint4* out,
                 int32_t dv, float keep, float scale) {
-  using V = VecT<T>;
-  constexpr int N = V::N;
   extern __shared__ float4 sm4[];
-  float* sm = reinterpret_cast<float*>(sm4);
-  const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
   if ((int32_t)blockIdx.x < mid_blocks) {
     const int32_t k = blockIdx.x * (kFinThreads / 32) + (threadIdx.x >> 5);
     if (k >= n_mid) return;
-    const int4 ds = long_desc[k];
-    const int lane = threadIdx.x & 31;
-    const float sc = inv_norm ? scale * inv_norm[ds.x] : scale;
-    for (int col = lane; col < dv; col += 32) {
-      float tot[N], sf[N], r[N];
-      sum_chunks<N>(partials, ds.y, ds.z, dv, col, tot);
-      const size_t o = (size_t)ds.x * dv + col;
-      V::unpack(keep != 0.f ? self_in[o] : zero4, sf);
-#pragma unroll
-      for (int e = 0; e < N; ++e) r[e] = fmaf(keep, sf[e], sc * tot[e]);
-      out[o] = V::pack(r);
-    }
+    dev::finalize_mid<T>(long_desc[k], threadIdx.x & 31, partials, inv_norm, self_in, out, dv, keep,
+                         scale);
     return;
   }
   const int32_t k = n_mid + (int32_t)blockIdx.x - mid_blocks;
   if (k >= n_mid + n_huge) return;
-  const int4 ds = long_desc[k];
-  const int S = (int)blockDim.x / dv;
-  const int t = threadIdx.x;
-  const int slice = t / dv;
-  const int col = t - slice * dv;
-  if (slice < S) {
-    const int32_t a = (int32_t)((int64_t)ds.z * slice / S);
-    const int32_t b = (int32_t)((int64_t)ds.z * (slice + 1) / S);
-    float part[N];
-    sum_chunks<N>(partials, ds.y + a, b - a, dv, col, part);
-#pragma unroll
-    for (int e = 0; e < N; ++e) sm[((size_t)slice * dv + col) * N + e] = part[e];
-  }
-  __syncthreads();
-  if (slice == 0) {
-    float tot[N], sf[N], r[N];
-#pragma unroll
-    for (int e = 0; e < N; ++e) tot[e] = sm[(size_t)col * N + e];
-    for (int q = 1; q < S; ++q)
-#pragma unroll
-      for (int e = 0; e < N; ++e) tot[e] += sm[((size_t)q * dv + col) * N + e];
-    const size_t o = (size_t)ds.x * dv + col;
-    V::unpack(keep != 0.f ? self_in[o] : zero4, sf);
-    const float sc = inv_norm ? scale * inv_norm[ds.x] : scale;
-#pragma unroll
-    for (int e = 0; e < N; ++e) r[e] = fmaf(keep, sf[e], sc * tot[e]);
-    out[o] = V::pack(r);
-  }
+  dev::finalize_huge<T>(long_desc[k], reinterpret_cast<float*>(sm4), partials, inv_norm, self_in,
+                        out, dv, keep, scale);
 }
 
 // Out-of-place sweeps (Jacobi): rows without neighbours carry over.
@@ -501,15 +275,21 @@ int ensure_scratch(float** p, size_t* have, size_t need, cudaStream_t s) {
 int refine_level(hnv_graph* g, int level, void* z_v, void* z_e, int dtype, int d, float omega,
                  int sweeps, int mode, cudaStream_t s) {
   Level& lv = g->levels[level];
-  const int64_t chunks = lv.planE.n_chunks > lv.planV.n_chunks ? lv.planE.n_chunks : lv.planV.n_chunks;
+  const size_t es = elem_size(dtype);
+  const SplitPlan* planE = &lv.planE;
+  const SplitPlan* planV = &lv.planV;
+  if (!use_tma(d)) {
+    HNV_CHECK(side_plan(g, &lv, 0, es * (size_t)d, &planE, s));
+    HNV_CHECK(side_plan(g, &lv, 1, es * (size_t)d, &planV, s));
+  }
+  const int64_t chunks = planE->n_chunks > planV->n_chunks ? planE->n_chunks : planV->n_chunks;
   HNV_CHECK(ensure_scratch(&g->partials, &g->partials_bytes,
                            sizeof(float) * (size_t)(chunks > 0 ? chunks : 1) * d, s));
-  const size_t es = elem_size(dtype);
   if (mode == HNV_SWEEP_JACOBI)
     HNV_CHECK(ensure_scratch(&g->jacobi_tmp, &g->jacobi_bytes,
                              es * ((size_t)lv.m > 0 ? lv.m : 1) * d, s));
-  const HalfSweep E{lv.e_nodes, nullptr, lv.inv_size_e, &lv.planE, lv.n, lv.m, g->d_err};
-  const HalfSweep V{lv.v_edges, lv.v_w, lv.inv_deg_v, &lv.planV, lv.m, lv.n, g->d_err};
+  const HalfSweep E{lv.e_nodes, nullptr, lv.inv_size_e, planE, lv.n, lv.m, g->d_err};
+  const HalfSweep V{lv.v_edges, lv.v_w, lv.inv_deg_v, planV, lv.m, lv.n, g->d_err};
   const double n = lv.n, m = lv.m, nnz = (double)lv.nnz;
   const double bytesE = (double)es * (n * d + 2.0 * m * d) + 4.0 * (nnz + 2.0 * m + 1.0);
   const double bytesV = (double)es * (m * d + 2.0 * n * d) + 4.0 * (2.0 * nnz + 2.0 * n + 1.0);

@@ -42,6 +42,8 @@ static std::atomic<int64_t> g_launches{0};
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+void note_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
 int num_sms() {
   static int cached = 0;
   if (cached == 0) {
