@@ -181,26 +181,78 @@ def oracle_threads() -> int:
 # the GPU arm
 # ---------------------------------------------------------------------------
 
-def source_hash(path):
-    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+TRAFFIC_SOURCES = ("paper_2103_09660_gb300/csrc/refine.cu",
+                   "paper_2103_09660_gb300/csrc/refine_device.cuh",
+                   "paper_2103_09660_gb300/csrc/incidence.cu")
+TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "traffic_refine_planted_1m.md")
+
+
+def source_hash():
+    """Hash of the sources that decide the refinement kernels' DRAM traffic
+    (the gather and reduction kernels and the work plans)."""
+    h = hashlib.sha256()
+    for rel in TRAFFIC_SOURCES:
+        h.update(open(os.path.join(ROOT, rel), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def load_traffic(kernel_tag):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source; else None."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
-    if not os.path.exists(p):
+    """DRAM bytes per half-sweep from the committed ncu summary (its JSON
+    block), if it was taken on the current kernel sources; else None."""
+    if not os.path.exists(TRAFFIC_SUMMARY):
         return None
     try:
-        rec = json.load(open(p)).get(kernel_tag)
-    except (OSError, ValueError):
+        text = open(TRAFFIC_SUMMARY).read()
+        block = text.split("```json", 1)[1].split("```", 1)[0]
+        rec = json.loads(block).get(kernel_tag)
+    except (OSError, ValueError, IndexError):
         return None
-    if not rec:
-        return None
-    src = os.path.join(ROOT, "paper_2103_09660_gb300", "csrc", "refine.cu")
-    if rec.get("source_sha256_16") != source_hash(src):
+    if not rec or rec.get("source_sha256_16") != source_hash():
         return None
     return rec.get("dram_bytes_per_launch")
+
+
+def traffic_summary(csv_path):
+    """Reads an ncu CSV of gpu__time_duration.sum, dram__bytes_read.sum and
+    dram__bytes_write.sum over whole V-cycles and prints, per refinement
+    side, the DRAM bytes and time per half-sweep (a half-sweep is the run of
+    that side's gather launches plus its split-row reduction)."""
+    import csv
+    rows = list(csv.reader(open(csv_path)))
+    hdr = next(i for i, r in enumerate(rows) if "Kernel Name" in r and "Metric Name" in r)
+    h = rows[hdr]
+    ii, ki, mi, vi = (h.index("ID"), h.index("Kernel Name"), h.index("Metric Name"),
+                      h.index("Metric Value"))
+    launches = {}
+    for r in rows[hdr + 1:]:
+        if len(r) <= vi:
+            continue
+        rec = launches.setdefault(int(r[ii]), {"name": r[ki]})
+        rec[r[mi]] = float(r[vi].replace(",", ""))
+    acc = {"E": [0.0, 0.0, 0], "V": [0.0, 0.0, 0]}
+    phase = None
+    for lid in sorted(launches):
+        rec = launches[lid]
+        name = rec["name"]
+        if "gather_kernel<" in name and "batched" not in name:
+            side = "V" if name.split("<", 1)[1].split(">", 1)[0].rstrip().endswith("1") else "E"
+            if side != phase:
+                acc[side][2] += 1
+            phase = side
+        elif "finalize_kernel<" in name and phase is not None and "batched" not in name:
+            side = phase
+        else:
+            phase = None
+            continue
+        acc[side][0] += rec.get("dram__bytes_read.sum", 0.0) + rec.get("dram__bytes_write.sum", 0.0)
+        acc[side][1] += rec.get("gpu__time_duration.sum", 0.0)
+    out = {}
+    for side, tag in (("E", "refine_e_half_sweep"), ("V", "refine_v_half_sweep")):
+        b, t, n = acc[side]
+        if n:
+            out[tag] = {"dram_bytes_per_launch": round(b / n), "ncu_us_per_launch": round(t / n / 1e3, 1),
+                        "half_sweeps": n, "source_sha256_16": source_hash()}
+    print(json.dumps(out, indent=1))
 
 
 def measured_peaks():
@@ -329,8 +381,12 @@ def run_ours(args, ws, rank, local):
     peak = float(peaks.get("hbm_gbs", 6800.0))
     tag = "refine_v_half_sweep" if dom == "refine_v" else "refine_e_half_sweep"
     traffic = load_traffic(tag)
+    n_half = phases[dom]["launches"]          # half-sweeps over the timed steps
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
+                "alg_bytes_per_launch": round(phases[dom]["alg_bytes"] / max(n_half, 1)),
+                "launch": "one half-sweep of one level (its gather launches and split-row "
+                          "reduction), averaged over the levels of the V-cycle",
                 "kernel": tag + " (gather_kernel + finalize_kernel)",
                 "peak_source": peak_src + " hbm_gbs (copy bandwidth)",
                 "bytes": "compulsory: neighbour table once, own rows read+written, indices, "
@@ -591,6 +647,57 @@ def run_autograd_study(args):
         "forward_ms": t_fwd, "forward_backward_ms": t_fb, "ratio": t_fb / t_fwd}))
 
 
+def run_feature_study(args):
+    """Feature rule (cosine, Section 3.1) against the hash rule on the same
+    hypergraph: coarsening time (CUDA events), levels, sizes, and how well
+    the first level's coarse nodes keep the planted communities together
+    (purity: the share of nodes whose coarse node's majority community is
+    their own). GPU only; the bit-exact comparison with the oracle is
+    tests/test_gpu_features.py."""
+    import torch
+    import paper_2103_09660_gb300 as H
+    from paper_2103_09660_gb300 import build as B
+    B.build()
+    spec = hypergen.CONFIGS[args.workload]
+    hg = hypergen.generate(spec)
+    X = hypergen.planted_features(hg, args.feature_dim, sigma=args.feature_sigma, seed=spec.seed)
+    dev = torch.device("cuda", 0)
+    Xd = torch.from_numpy(X).to(dev)
+    labels = hg.labels.astype(np.int64)
+
+    def purity(rep):
+        n2 = int(rep.max()) + 1
+        C = int(labels.max()) + 1
+        tab = np.zeros((n2, C), dtype=np.int64)
+        np.add.at(tab, (rep, labels), 1)
+        return float(tab.max(axis=1).sum() / labels.size)
+
+    out = {"study": "feature rule vs hash rule (coarsening)", "workload": args.workload,
+           "n": hg.n, "m": hg.m, "nnz": hg.nnz, "feature_dim": args.feature_dim,
+           "feature_sigma": args.feature_sigma, "min_nodes": spec.min_nodes,
+           "max_levels": spec.max_levels}
+    with H.Graph.from_hypergraph(hg, on_device=True) as G:
+        G.set_node_features(Xd)
+        for name, policy in (("hash", H.ASSIGN_HASH), ("cosine", H.ASSIGN_COSINE)):
+            ts = []
+            for _ in range(max(args.steps, 1) + 1):
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                L = G.coarsen(policy=policy, seed=spec.seed, min_nodes=spec.min_nodes,
+                              max_levels=spec.max_levels)
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            sizes = [G.level_info(l)[:2] for l in range(L)]
+            rep0 = G.level_array(0, H.ARR_REP_V).astype(np.int64) if L > 1 else None
+            out[name] = {"coarsen_ms": float(np.median(ts[1:])), "levels": L,
+                         "level_sizes": sizes,
+                         "level1_purity": purity(rep0) if rep0 is not None else None}
+        G.sync_status()
+    print(json.dumps(out))
+
+
 def run_batch_study(args):
     """The batching workload (256 planted hypergraphs, 1K..100K nodes, d=64):
     the V-cycle of every graph looped through the single-graph path (FP32 and
@@ -703,6 +810,12 @@ def main(argv=None):
                     help="embedding storage of the timed V-cycle (sums are float32 either way)")
     ap.add_argument("--precision-study", action="store_true",
                     help="BF16 vs FP32 per level and V-cycle time (use with --workload planted_4m)")
+    ap.add_argument("--traffic-summary", default=None, metavar="NCU_CSV",
+                    help="print DRAM bytes per refinement half-sweep from an ncu CSV")
+    ap.add_argument("--feature-study", action="store_true",
+                    help="feature (cosine) vs hash coarsening on the workload")
+    ap.add_argument("--feature-dim", type=int, default=32)
+    ap.add_argument("--feature-sigma", type=float, default=1.0)
     ap.add_argument("--batch-study", action="store_true",
                     help="batched V-cycle over many hypergraphs vs looping the single-graph path")
     ap.add_argument("--batch-count", type=int, default=256)
@@ -721,6 +834,12 @@ def main(argv=None):
         return
     if args.batch_study:
         run_batch_study(args)
+        return
+    if args.feature_study:
+        run_feature_study(args)
+        return
+    if args.traffic_summary:
+        traffic_summary(args.traffic_summary)
         return
     if args.impl == "reference":
         line = run_reference(args, ws, rank, local)

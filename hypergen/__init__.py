@@ -132,6 +132,19 @@ def batch_specs(count: int = 256, n_min: int = 1_000, n_max: int = 100_000,
             for i, n in enumerate(ns)]
 
 
+def planted_features(hg: Hypergraph, k: int, sigma: float = 1.0, seed: int = 0) -> np.ndarray:
+    """Node features for feature-based coarsening: planted-community
+    Gaussians. Each community c draws a centre mu_c ~ N(0, I_k); node v gets
+    mu_{label(v)} + sigma * N(0, I_k). float32 [n, k]. Seeded."""
+    if hg.labels is None:
+        raise ValueError("planted features need community labels")
+    rng = np.random.default_rng([seed, 0xFEA7])
+    C = int(hg.labels.max()) + 1 if hg.n else 0
+    mu = rng.standard_normal((C, k))
+    noise = rng.standard_normal((hg.n, k))
+    return (mu[hg.labels] + sigma * noise).astype(np.float32)
+
+
 def _first_occurrences(keys: np.ndarray) -> np.ndarray:
     """Indices of the first occurrence of each distinct value of ``keys``."""
     order = np.argsort(keys, kind="stable")

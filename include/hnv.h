@@ -76,7 +76,16 @@ typedef enum {
   HNV_ASSIGN_HASH = 0,
   HNV_ASSIGN_LOW_DEGREE = 1,
   HNV_ASSIGN_HIGH_WEIGHT = 2,
-  HNV_ASSIGN_EXPLICIT = 3
+  HNV_ASSIGN_EXPLICIT = 3,
+  /* Feature rule of Section 3.1 (nodes with features): f(e) = mean of its
+   * members' features, c(v) = argmax_{e in N(v)} cos(f(e), f(v)), ties to
+   * the smallest (hash priority, e) as under HNV_ASSIGN_HASH; a zero norm
+   * gives score 0. The cosines are float32 with every operation rounded
+   * separately (no fused multiply-add), sums in a fixed order: products
+   * and squares added in dimension order, members in ascending node order.
+   * Merged nodes take the mean of their nodes' features (ascending node
+   * order), which the next level uses. Needs hnv_set_node_features. */
+  HNV_ASSIGN_COSINE = 4
 } hnv_assign;
 
 typedef struct {
@@ -159,6 +168,27 @@ typedef enum {
  * else host) and synchronises the stream. capacity_bytes guards dst. */
 int hnv_copy_level_array(const hnv_graph* g, int level, int which, void* dst,
                          size_t capacity_bytes, int dst_on_device, hnv_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Node features for the feature rule (HNV_ASSIGN_COSINE, Section 3.1: the
+ * node feature matrix X of Algorithm 1's input and its coarse version X').
+ *
+ * hnv_set_node_features: copies X [n_0 x k] (row-major float32, host or
+ * device per x_on_device) into the graph as level 0's features, replacing
+ * any earlier ones. Every value must be finite with |x| <= 1e15 (so no sum
+ * of squares can overflow): otherwise HNV_ERR_INVALID_ARG and nothing
+ * changes. 1 <= k <= 4096. Synchronises the stream. A later hnv_coarsen
+ * with HNV_ASSIGN_COSINE computes every coarse level's features.
+ *
+ * hnv_copy_level_features: copies level `level`'s features [n_l x k] to
+ * dst (host or device); HNV_ERR_STATE if that level has none.
+ * hnv_level_feature_dim: k of that level's features, 0 if none.
+ * ------------------------------------------------------------------------- */
+int hnv_set_node_features(hnv_graph* g, const float* x, int32_t k, int x_on_device,
+                          hnv_stream_t stream);
+int hnv_copy_level_features(const hnv_graph* g, int level, float* dst, size_t capacity_bytes,
+                            int dst_on_device, hnv_stream_t stream);
+int hnv_level_feature_dim(const hnv_graph* g, int level, int32_t* k);
 
 /* ---------------------------------------------------------------------------
  * hnv_project -- initial embedding of level fine_level from level

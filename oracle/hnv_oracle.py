@@ -49,6 +49,11 @@ ASSIGN_HASH = 0
 ASSIGN_LOW_DEGREE = 1
 ASSIGN_HIGH_WEIGHT = 2
 ASSIGN_EXPLICIT = 3
+ASSIGN_COSINE = 4
+
+# Feature values are checked against this bound so that no sum of squares
+# can overflow float32 (|x| <= 1e15: x^2 <= 1e30, and up to 2^24 of them).
+FEATURE_ABS_MAX = 1e15
 
 SWEEP_TWO_PHASE = 0
 SWEEP_JACOBI = 1
@@ -206,6 +211,8 @@ class CoarsenParams:
     # ASSIGN_EXPLICIT: uint64 table [max_levels, m0]; entry [l, orig_e(e)]
     # is the priority of hyperedge e at level l (test-only policy).
     explicit_prio: Optional[np.ndarray] = None
+    # ASSIGN_COSINE: level-0 node features, float32 [n0, k].
+    features: Optional[np.ndarray] = None
 
 
 def priorities(lv: Level, params: CoarsenParams, level: int) -> np.ndarray:
@@ -252,8 +259,104 @@ def assign_hyperedges(lv: Level, prio: np.ndarray) -> np.ndarray:
     return c
 
 
-def coarsen_level(lv: Level, params: CoarsenParams, level: int
-                  ) -> Tuple[np.ndarray, np.ndarray, Level]:
+# ---------------------------------------------------------------------------
+# Feature-based assignment (Section 3.1, nodes with features)
+#
+# The choice of c(v) is an argmax over floating-point scores, so it is taken
+# in float32 with every rounding step written out, in the order the GPU
+# kernels use: sums run one term at a time in a fixed order, products and
+# quotients are rounded separately (no fused multiply-add), square roots
+# are IEEE-rounded. numpy float32 arithmetic rounds each operation, so the
+# float32 steps below are that definition.
+# ---------------------------------------------------------------------------
+
+def check_features(X: np.ndarray, n: int) -> np.ndarray:
+    """Level-0 node features as float32 [n, k], k >= 1, finite, |x| <= 1e15."""
+    X = np.asarray(X)
+    if X.ndim != 2 or X.shape[0] != n or X.shape[1] < 1:
+        raise ValueError("features must be [n, k] with k >= 1")
+    X = X.astype(np.float32)
+    if not np.all(np.isfinite(X)) or np.any(np.abs(X) > FEATURE_ABS_MAX):
+        raise ValueError("features must be finite with |x| <= 1e15")
+    return X
+
+
+def segment_means_f32(ptr: np.ndarray, idx: np.ndarray, X: np.ndarray) -> np.ndarray:
+    """Row r of the result: the float32 mean of X[idx[ptr[r]:ptr[r+1]]],
+    summed one row at a time in list order, then divided by the count (a
+    row with an empty list is 0)."""
+    rows = ptr.size - 1
+    k = X.shape[1]
+    cnt = np.diff(ptr)
+    acc = np.zeros((rows, k), dtype=np.float32)
+    for j in range(int(cnt.max()) if rows else 0):
+        sel = np.nonzero(cnt > j)[0]
+        acc[sel] = acc[sel] + X[idx[ptr[sel] + j]]
+    den = np.maximum(cnt, 1).astype(np.float32)
+    return (acc / den[:, None]).astype(np.float32)
+
+
+def row_norms_f32(F: np.ndarray) -> np.ndarray:
+    """sqrt(sum_i F[:, i] * F[:, i]), squares added in dimension order."""
+    acc = np.zeros(F.shape[0], dtype=np.float32)
+    for i in range(F.shape[1]):
+        acc = acc + F[:, i] * F[:, i]
+    return np.sqrt(acc).astype(np.float32)
+
+
+def edge_features(lv: Level, X: np.ndarray) -> np.ndarray:
+    """ComputeEdgeFeature (Algorithm 1, Section 3.1): the feature vector of a
+    hyperedge is the mean of its members' features (members in ascending
+    node order)."""
+    return segment_means_f32(lv.e_ptr, lv.e_nodes, X)
+
+
+def cosine_scores(lv: Level, X: np.ndarray, FE: np.ndarray) -> np.ndarray:
+    """cos(f(e), f(v)) = f(e).f(v) / (|f(e)| |f(v)|) for every incidence, in
+    CSC order (node-major, ascending hyperedge). READING: where either norm
+    is 0 the cosine is undefined; its score is taken as 0."""
+    node_of = row_of(lv.v_ptr)
+    edge = lv.v_edges
+    dot = np.zeros(edge.size, dtype=np.float32)
+    for i in range(X.shape[1]):
+        dot = dot + FE[edge, i] * X[node_of, i]
+    den = row_norms_f32(FE)[edge] * row_norms_f32(X)[node_of]
+    score = np.zeros(edge.size, dtype=np.float32)
+    ok = den > 0
+    score[ok] = dot[ok] / den[ok]
+    return score
+
+
+def assign_cosine(lv: Level, X: np.ndarray, prio: np.ndarray) -> np.ndarray:
+    """AssignHyperedge with features: ``c(v) = argmax_{e in N(v)} cos(f(e),
+    f(v))``. READING of the tie rule (the paper picks at random): among
+    equal scores the smallest ``(prio(e), e)`` wins, the same per-level hash
+    order as the featureless rule. ``-1`` if ``N(v)`` is empty."""
+    c = np.full(lv.n, -1, dtype=np.int64)
+    if lv.nnz == 0:
+        return c
+    score = cosine_scores(lv, X, edge_features(lv, X))
+    node_of = row_of(lv.v_ptr)
+    edge = lv.v_edges
+    order = np.lexsort((edge, prio[edge], -score, node_of))
+    first = np.ones(order.size, dtype=bool)
+    first[1:] = node_of[order][1:] != node_of[order][:-1]
+    c[node_of[order][first]] = edge[order][first]
+    return c
+
+
+def merge_features(rep_v: np.ndarray, n2: int, X: np.ndarray) -> np.ndarray:
+    """Coarse node features X' (Algorithm 1's output). READING (the merge rule
+    is not stated): the mean of the merged nodes' features, in ascending
+    fine-node order."""
+    order = np.argsort(rep_v, kind="stable")
+    ptr = np.zeros(n2 + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rep_v, minlength=n2), out=ptr[1:])
+    return segment_means_f32(ptr, order, X)
+
+
+def coarsen_level(lv: Level, params: CoarsenParams, level: int,
+                  X: Optional[np.ndarray] = None) -> Tuple[np.ndarray, np.ndarray, Level]:
     """One coarsening step of Algorithm 1.
 
     Returns ``rep_v[n]`` (coarse node of each node), ``rep_e[m]`` (coarse
@@ -279,8 +382,12 @@ def coarsen_level(lv: Level, params: CoarsenParams, level: int
     4. addEdge(rep(e), rep(v)) for v in e: coarse members are the distinct
        ``rep_v`` of the members, ascending.
     """
-    prio = priorities(lv, params, level)
-    c = assign_hyperedges(lv, prio)
+    if params.policy == ASSIGN_COSINE:
+        prio = hash_priority(np.arange(lv.m, dtype=np.uint64), params.seed, level)
+        c = assign_cosine(lv, X, prio)
+    else:
+        prio = priorities(lv, params, level)
+        c = assign_hyperedges(lv, prio)
     key = np.where(c >= 0, c, lv.m + np.arange(lv.n, dtype=np.int64))
     uniq = np.unique(key)
     rep_v = np.searchsorted(uniq, key).astype(np.int64)
@@ -320,6 +427,8 @@ class Hierarchy:
     levels: List[Level]
     rep_v: List[np.ndarray]     # rep_v[l]: level l -> level l+1
     rep_e: List[np.ndarray]
+    # ASSIGN_COSINE: node features of every level (float32 [n_l, k])
+    features: Optional[List[np.ndarray]] = None
 
 
 def coarsen(lv0: Level, params: CoarsenParams) -> Hierarchy:
@@ -333,18 +442,25 @@ def coarsen(lv0: Level, params: CoarsenParams) -> Hierarchy:
     levels = [lv0]
     rv: List[np.ndarray] = []
     re: List[np.ndarray] = []
+    feats = None
+    if params.policy == ASSIGN_COSINE:
+        if params.features is None:
+            raise ValueError("the cosine policy needs node features")
+        feats = [check_features(params.features, lv0.n)]
     while True:
         cur = levels[-1]
         ell = len(levels) - 1
         if not (cur.n > params.min_nodes and ell < params.max_levels and cur.m > 0):
             break
-        rep_v, rep_e, nxt = coarsen_level(cur, params, ell)
+        rep_v, rep_e, nxt = coarsen_level(cur, params, ell, feats[-1] if feats else None)
         if nxt.n == cur.n:
             break
         levels.append(nxt)
         rv.append(rep_v)
         re.append(rep_e)
-    return Hierarchy(levels=levels, rep_v=rv, rep_e=re)
+        if feats is not None:
+            feats.append(merge_features(rep_v, nxt.n, feats[-1]))
+    return Hierarchy(levels=levels, rep_v=rv, rep_e=re, features=feats)
 
 
 # ---------------------------------------------------------------------------

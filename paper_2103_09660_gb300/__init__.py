@@ -29,14 +29,15 @@ __all__ = [
     "PHASE_BUILD", "PHASE_COARSEN", "PHASE_PROJECT", "PHASE_REFINE_E", "PHASE_REFINE_V",
     "Graph", "hnv_build_incidence", "hnv_coarsen", "hnv_project", "hnv_refine",
     "hnv_vcycle", "hnv_refine_noalloc", "hnv_set_weights", "hnv_checkpoint_floats",
-    "hnv_vcycle_save", "hnv_vcycle_backward", "vcycle_autograd", "Batch", "kernel_launch_count", "timing_enable", "timing_reset", "timing_read",
+    "hnv_vcycle_save", "hnv_vcycle_backward", "vcycle_autograd", "Batch", "kernel_launch_count",
+    "hnv_set_node_features", "hnv_copy_level_features", "timing_enable", "timing_reset", "timing_read",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 library_path = os.path.join(_HERE, "libhnv.so")
 
 # enums of include/hnv.h
-ASSIGN_HASH, ASSIGN_LOW_DEGREE, ASSIGN_HIGH_WEIGHT, ASSIGN_EXPLICIT = 0, 1, 2, 3
+ASSIGN_HASH, ASSIGN_LOW_DEGREE, ASSIGN_HIGH_WEIGHT, ASSIGN_EXPLICIT, ASSIGN_COSINE = 0, 1, 2, 3, 4
 SWEEP_TWO_PHASE, SWEEP_JACOBI = 0, 1
 F32, BF16 = 0, 1
 (ARR_E_PTR, ARR_E_NODES, ARR_V_PTR, ARR_V_EDGES, ARR_W, ARR_REP_V, ARR_REP_E,
@@ -92,6 +93,10 @@ def _declare(L):
         "hnv_refine_noalloc": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_int, f32, ctypes.c_int, _P]),
         "hnv_graph_free": (None, [_P]),
         "hnv_sync_status": (ctypes.c_int, [_P, _P]),
+        "hnv_set_node_features": (ctypes.c_int, [_P, _P, i32, ctypes.c_int, _P]),
+        "hnv_copy_level_features": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t,
+                                                   ctypes.c_int, _P]),
+        "hnv_level_feature_dim": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(i32)]),
         "hnv_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), i32, ctypes.POINTER(_P)]),
         "hnv_batch_offsets": (ctypes.c_int, [_P, _P, _P, _P]),
         "hnv_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, f32, ctypes.POINTER(BatchTuning)]),
@@ -202,6 +207,36 @@ def hnv_coarsen(g: int, policy: int = ASSIGN_HASH, seed: int = 0, min_nodes: int
     out = ctypes.c_int32()
     _check(lib().hnv_coarsen(g, ctypes.byref(prm), ctypes.byref(out)), "hnv_coarsen")
     return out.value
+
+
+def hnv_set_node_features(g: int, x, stream=None):
+    """Level-0 node features (float32 [n0, k]): a numpy array (host) or a
+    CUDA tensor (device)."""
+    import torch
+    if isinstance(x, torch.Tensor) and x.is_cuda:
+        if x.dtype != torch.float32 or x.dim() != 2 or not x.is_contiguous():
+            raise TypeError("features must be a contiguous float32 [n, k] tensor")
+        _check(lib().hnv_set_node_features(g, x.data_ptr(), int(x.shape[1]), 1,
+                                           _stream_handle(stream)), "hnv_set_node_features")
+        return
+    a = np.ascontiguousarray(x, dtype=np.float32)
+    if a.ndim != 2:
+        raise TypeError("features must be [n, k]")
+    _check(lib().hnv_set_node_features(g, a.ctypes.data, int(a.shape[1]), 0,
+                                       _stream_handle(stream)), "hnv_set_node_features")
+
+
+def hnv_copy_level_features(g: int, level: int, stream=None) -> np.ndarray:
+    """Host copy of a level's node features (float32 [n_l, k])."""
+    k = ctypes.c_int32()
+    _check(lib().hnv_level_feature_dim(g, level, ctypes.byref(k)), "hnv_level_feature_dim")
+    n, m, nnz = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    _check(lib().hnv_level_info(g, level, ctypes.byref(n), ctypes.byref(m), ctypes.byref(nnz)),
+           "hnv_level_info")
+    out = np.empty((n.value, max(k.value, 1)), dtype=np.float32)
+    _check(lib().hnv_copy_level_features(g, level, out.ctypes.data, out.nbytes, 0,
+                                         _stream_handle(stream)), "hnv_copy_level_features")
+    return out
 
 
 def hnv_project(g: int, fine_level: int, zc_v, zc_e, zf_v, zf_e, stream=None):
@@ -430,6 +465,12 @@ class Graph:
 
     def set_weights(self, w0):
         hnv_set_weights(self.handle, w0, self.stream)
+
+    def set_node_features(self, x):
+        hnv_set_node_features(self.handle, x, self.stream)
+
+    def level_features(self, level: int) -> np.ndarray:
+        return hnv_copy_level_features(self.handle, level, self.stream)
 
     def coarsen(self, **kw) -> int:
         return hnv_coarsen(self.handle, **kw)

@@ -57,6 +57,15 @@ int check_embedding_args(hnv_dtype dt, int d) {
 
 size_t dtype_size(hnv_dtype dt) { return dt == HNV_BF16 ? 2 : 4; }
 
+__global__ void check_features_kernel(int64_t count, const float* __restrict__ x,
+                                      int32_t* __restrict__ err) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float v = x[i];
+    if (!(fabsf(v) <= 1e15f)) atomicOr(err, (int32_t)ERRBIT_BAD_FEATURE);   // also NaN
+  }
+}
+
 int check_buf(const void* p, int64_t rows, const char* name) {
   if (rows > 0 && p == nullptr) HNV_FAIL(HNV_ERR_INVALID_ARG, "%s is NULL", name);
   if (p && (reinterpret_cast<uintptr_t>(p) & 15u))
@@ -238,8 +247,10 @@ int hnv_build_incidence(int32_t n_nodes, int32_t n_edges, const int64_t* edge_pt
 int hnv_coarsen(hnv_graph* g, const hnv_coarsen_params* p, int32_t* n_levels) {
   clear_error_detail();
   if (!g || !p) HNV_FAIL(HNV_ERR_INVALID_ARG, "graph or params is NULL");
-  if (p->policy < HNV_ASSIGN_HASH || p->policy > HNV_ASSIGN_EXPLICIT)
+  if (p->policy < HNV_ASSIGN_HASH || p->policy > HNV_ASSIGN_COSINE)
     HNV_FAIL(HNV_ERR_INVALID_ARG, "unknown policy %d", p->policy);
+  if (p->policy == HNV_ASSIGN_COSINE && !g->levels[0].feat)
+    HNV_FAIL(HNV_ERR_STATE, "the cosine policy needs node features (hnv_set_node_features)");
   if (p->max_levels < 0) HNV_FAIL(HNV_ERR_INVALID_ARG, "max_levels < 0");
   if (p->policy == HNV_ASSIGN_EXPLICIT && !p->explicit_prio && p->max_levels > 0)
     HNV_FAIL(HNV_ERR_INVALID_ARG, "EXPLICIT policy needs explicit_prio");
@@ -353,6 +364,74 @@ int hnv_copy_level_array(const hnv_graph* g, int level, int which, void* dst,
   HNV_CUDA(cudaMemcpyAsync(dst, src, bytes,
                            dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
   HNV_CUDA(cudaStreamSynchronize(s));
+  return HNV_OK;
+}
+
+int hnv_set_node_features(hnv_graph* g, const float* x, int32_t k, int x_on_device,
+                          hnv_stream_t stream) {
+  clear_error_detail();
+  if (!g) HNV_FAIL(HNV_ERR_INVALID_ARG, "graph is NULL");
+  if (k < 1 || k > 4096) HNV_FAIL(HNV_ERR_INVALID_ARG, "k = %d not in [1, 4096]", k);
+  Level& l0 = g->levels[0];
+  if (l0.n > 0 && !x) HNV_FAIL(HNV_ERR_INVALID_ARG, "features are NULL");
+  DeviceGuard dgd(g->device);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const size_t bytes = sizeof(float) * (size_t)l0.n * k;
+  float* feat = nullptr;
+  HNV_CHECK(dev_alloc((void**)&feat, bytes ? bytes : 16, s));
+  int rc = HNV_OK;
+  if (bytes) {
+    const cudaError_t e = cudaMemcpyAsync(feat, x, bytes,
+                                          x_on_device ? cudaMemcpyDeviceToDevice
+                                                      : cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) rc = cuda_status(e, "cudaMemcpyAsync");
+  }
+  if (rc == HNV_OK && bytes)
+    rc = launch("check_features", check_features_kernel, grid_for((int64_t)l0.n * k, 256), 256, 0,
+                s, (int64_t)l0.n * k, (const float*)feat, g->d_err);
+  int32_t bits = 0;
+  if (rc == HNV_OK) rc = read_and_clear_err(g, s, &bits);
+  if (rc == HNV_OK && (bits & ERRBIT_BAD_FEATURE)) {
+    rc = HNV_ERR_INVALID_ARG;
+    set_error_detail("features must be finite with |x| <= 1e15");
+  }
+  if (rc != HNV_OK) {
+    dev_free(feat, s);
+    return rc;
+  }
+  drop_owned(&l0, l0.feat, s);
+  l0.feat = feat;
+  l0.feat_k = k;
+  l0.owned.push_back(feat);
+  return HNV_OK;
+}
+
+int hnv_copy_level_features(const hnv_graph* g, int level, float* dst, size_t capacity_bytes,
+                            int dst_on_device, hnv_stream_t stream) {
+  clear_error_detail();
+  if (!g) HNV_FAIL(HNV_ERR_INVALID_ARG, "graph is NULL");
+  if (level < 0 || level >= (int)g->levels.size())
+    HNV_FAIL(HNV_ERR_OUT_OF_RANGE, "level %d not in [0, %d)", level, (int)g->levels.size());
+  const Level& lv = g->levels[level];
+  if (!lv.feat) HNV_FAIL(HNV_ERR_STATE, "level %d has no node features", level);
+  const size_t bytes = sizeof(float) * (size_t)lv.n * lv.feat_k;
+  if (bytes > capacity_bytes)
+    HNV_FAIL(HNV_ERR_INVALID_ARG, "destination too small (%zu < %zu)", capacity_bytes, bytes);
+  if (bytes == 0) return HNV_OK;
+  if (!dst) HNV_FAIL(HNV_ERR_INVALID_ARG, "dst is NULL");
+  DeviceGuard dgd(g->device);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  HNV_CUDA(cudaMemcpyAsync(dst, lv.feat, bytes,
+                           dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  HNV_CUDA(cudaStreamSynchronize(s));
+  return HNV_OK;
+}
+
+int hnv_level_feature_dim(const hnv_graph* g, int level, int32_t* k) {
+  if (!g || !k) HNV_FAIL(HNV_ERR_INVALID_ARG, "NULL argument");
+  if (level < 0 || level >= (int)g->levels.size())
+    HNV_FAIL(HNV_ERR_OUT_OF_RANGE, "level %d not in [0, %d)", level, (int)g->levels.size());
+  *k = g->levels[level].feat ? g->levels[level].feat_k : 0;
   return HNV_OK;
 }
 

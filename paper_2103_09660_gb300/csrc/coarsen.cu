@@ -3,6 +3,8 @@
 // hyperedge merge into one coarse node, hyperedges whose members all merged
 // into one coarse node are removed, the rest connect the coarse nodes of
 // their members.
+#include <cmath>
+
 #include "hnv_internal.cuh"
 
 namespace hnv {
@@ -43,23 +45,95 @@ __global__ void priority_kernel(int32_t m, int32_t policy, uint64_t salt,
   }
 }
 
-// c(v) = argmin_{e in N(v)} (prio(e), e), or -1; warp per node, lanes stride
-// the CSC row, then a lexicographic min over the warp. Rows longer than
-// kLongRow go to `long_rows` for assign_long_kernel (block per row).
+// c(v) = argmin_{e in N(v)} (-score(v, e), prio(e), e), or -1; warp per
+// node, lanes stride the CSC row, then a lexicographic min over the warp.
+// score is the cosine of the feature rule (per CSC entry), or absent (all
+// equal: the featureless rules). Rows longer than kLongRow go to
+// `long_rows` for assign_long_kernel (block per row).
 constexpr int32_t kLongRow = 4096;
 constexpr int kLongThreads = 512;
 
-__device__ __forceinline__ void lex_min(uint64_t& bp, int32_t& be, uint64_t p, int32_t e) {
-  if (p < bp || (p == bp && e < be)) {
+__device__ __forceinline__ void lex_min(float& bs, uint64_t& bp, int32_t& be, float sc, uint64_t p,
+                                        int32_t e) {
+  if (sc > bs || (sc == bs && (p < bp || (p == bp && e < be)))) {
+    bs = sc;
     bp = p;
     be = e;
   }
 }
 
+// ---------------------------------------------------------------------------
+// Feature rule (Section 3.1, nodes with features). The cosine decides an
+// argmax, so every float step is an explicitly rounded float32 operation
+// (no fused multiply-add) in a fixed order; the oracle takes the same steps.
+// ---------------------------------------------------------------------------
+
+// out[r] = mean of X rows idx[ptr[r] .. ptr[r+1]) (one thread per (r, dim),
+// added in list order, then divided by the count; an empty list gives 0).
+__global__ void segment_mean_kernel(int32_t rows, int32_t k, const int32_t* __restrict__ ptr,
+                                    const int32_t* __restrict__ idx, const float* __restrict__ X,
+                                    float* __restrict__ out) {
+  const int64_t total = (int64_t)rows * k;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / k;
+    const int32_t i = (int32_t)(t - r * k);
+    const int32_t b = ptr[r], e = ptr[r + 1];
+    float acc = 0.f;
+    for (int32_t j = b; j < e; ++j) acc = __fadd_rn(acc, X[(size_t)idx[j] * k + i]);
+    out[t] = (e > b) ? __fdiv_rn(acc, (float)(e - b)) : 0.f;
+  }
+}
+
+// |F[r]| = sqrt(sum_i F[r,i] * F[r,i]), squares added in dimension order.
+__global__ void row_norm_kernel(int32_t rows, int32_t k, const float* __restrict__ F,
+                                float* __restrict__ out) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    float acc = 0.f;
+    for (int32_t i = 0; i < k; ++i) {
+      const float x = F[(size_t)r * k + i];
+      acc = __fadd_rn(acc, __fmul_rn(x, x));
+    }
+    out[r] = __fsqrt_rn(acc);
+  }
+}
+
+// node_of[j] = the node of CSC entry j (warp per node).
+__global__ void node_of_kernel(int32_t n, const int32_t* __restrict__ v_ptr,
+                               int32_t* __restrict__ node_of) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t v = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); v < n;
+       v += warps)
+    for (int32_t j = v_ptr[v] + lane; j < v_ptr[v + 1]; j += 32) node_of[j] = (int32_t)v;
+}
+
+// score[j] = cos(f(e), f(v)) for CSC entry j = (v, e): f(e).f(v) with the
+// products added in dimension order, over |f(e)| |f(v)|; 0 where that
+// product is 0 (an undefined cosine).
+__global__ void cosine_score_kernel(int64_t nnz, int32_t k, const int32_t* __restrict__ node_of,
+                                    const int32_t* __restrict__ v_edges,
+                                    const float* __restrict__ X, const float* __restrict__ FE,
+                                    const float* __restrict__ nv, const float* __restrict__ ne,
+                                    float* __restrict__ score) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nnz;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = node_of[j], e = v_edges[j];
+    const float* fv = X + (size_t)v * k;
+    const float* fe = FE + (size_t)e * k;
+    float dot = 0.f;
+    for (int32_t i = 0; i < k; ++i) dot = __fadd_rn(dot, __fmul_rn(fe[i], fv[i]));
+    const float den = __fmul_rn(ne[e], nv[v]);
+    score[j] = (den > 0.f) ? __fdiv_rn(dot, den) : 0.f;
+  }
+}
+
 __global__ void assign_kernel(int32_t n, const int32_t* __restrict__ v_ptr,
                               const int32_t* __restrict__ v_edges,
-                              const uint64_t* __restrict__ prio, int32_t* __restrict__ c,
-                              int32_t* __restrict__ long_rows, int32_t* __restrict__ n_long) {
+                              const uint64_t* __restrict__ prio, const float* __restrict__ score,
+                              int32_t* __restrict__ c, int32_t* __restrict__ long_rows,
+                              int32_t* __restrict__ n_long) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t v = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); v < n;
@@ -69,17 +143,19 @@ __global__ void assign_kernel(int32_t n, const int32_t* __restrict__ v_ptr,
       if (lane == 0) long_rows[atomicAdd(n_long, 1)] = (int32_t)v;
       continue;
     }
+    float bs = -INFINITY;
     uint64_t bp = ~0ull;
     int32_t be = 0x7fffffff;
     for (int64_t k = b + lane; k < end; k += 32) {
       const int32_t e = v_edges[k];
-      lex_min(bp, be, prio[e], e);
+      lex_min(bs, bp, be, score ? score[k] : 0.f, prio[e], e);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
+      const float os = __shfl_xor_sync(FULL, bs, o);
       const uint64_t op = __shfl_xor_sync(FULL, bp, o);
       const int32_t oe = __shfl_xor_sync(FULL, be, o);
-      lex_min(bp, be, op, oe);
+      lex_min(bs, bp, be, os, op, oe);
     }
     if (lane == 0) c[v] = (end > b) ? be : -1;
   }
@@ -88,7 +164,9 @@ __global__ void assign_kernel(int32_t n, const int32_t* __restrict__ v_ptr,
 __global__ void __launch_bounds__(kLongThreads)
 assign_long_kernel(const int32_t* __restrict__ long_rows, const int32_t* __restrict__ n_long,
                    const int32_t* __restrict__ v_ptr, const int32_t* __restrict__ v_edges,
-                   const uint64_t* __restrict__ prio, int32_t* __restrict__ c) {
+                   const uint64_t* __restrict__ prio, const float* __restrict__ score,
+                   int32_t* __restrict__ c) {
+  __shared__ float ss[kLongThreads / 32];
   __shared__ uint64_t sp[kLongThreads / 32];
   __shared__ int32_t se[kLongThreads / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -96,29 +174,38 @@ assign_long_kernel(const int32_t* __restrict__ long_rows, const int32_t* __restr
   for (int32_t i = blockIdx.x; i < count; i += gridDim.x) {
     const int32_t v = long_rows[i];
     const int64_t b = v_ptr[v], end = v_ptr[v + 1];
+    float bs = -INFINITY;
     uint64_t bp = ~0ull;
     int32_t be = 0x7fffffff;
     for (int64_t k = b + threadIdx.x; k < end; k += kLongThreads) {
       const int32_t e = v_edges[k];
-      lex_min(bp, be, prio[e], e);
+      lex_min(bs, bp, be, score ? score[k] : 0.f, prio[e], e);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
+      const float os = __shfl_xor_sync(FULL, bs, o);
       const uint64_t op = __shfl_xor_sync(FULL, bp, o);
       const int32_t oe = __shfl_xor_sync(FULL, be, o);
-      lex_min(bp, be, op, oe);
+      lex_min(bs, bp, be, os, op, oe);
     }
     if (lane == 0) {
+      ss[w] = bs;
       sp[w] = bp;
       se[w] = be;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      for (int q = 1; q < kLongThreads / 32; ++q) lex_min(bp, be, sp[q], se[q]);
+      for (int q = 1; q < kLongThreads / 32; ++q) lex_min(bs, bp, be, ss[q], sp[q], se[q]);
       c[v] = be;
     }
     __syncthreads();
   }
+}
+
+__global__ void iota_kernel(int64_t n, int32_t* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (int32_t)i;
 }
 
 // key(v) = c(v) or m + v; flags[key] = 1 (all writers store the same value).
@@ -307,17 +394,43 @@ int coarsen_step(hnv_graph* g, int level, const hnv_coarsen_params* p,
   HNV_CHECK(launch("priority", priority_kernel, grid_for(m, 256), 256, 0, s, m, p->policy, salt,
                    (const int32_t*)fine->e_ptr, (const float*)fine->w,
                    (const int32_t*)fine->orig_e, d_explicit, prio));
+  // the feature rule: a cosine per CSC entry
+  float* score = nullptr;
+  const int32_t k = fine->feat_k;
+  if (p->policy == HNV_ASSIGN_COSINE) {
+    if (!fine->feat || k < 1) HNV_FAIL(HNV_ERR_STATE, "level %d has no node features", level);
+    float *fe = nullptr, *nv = nullptr, *ne = nullptr;
+    int32_t* node_of = nullptr;
+    HNV_CHECK(pool.get(&fe, (size_t)m * k));
+    HNV_CHECK(pool.get(&nv, (size_t)n));
+    HNV_CHECK(pool.get(&ne, (size_t)m));
+    HNV_CHECK(pool.get(&node_of, (size_t)nnz));
+    HNV_CHECK(pool.get(&score, (size_t)nnz));
+    HNV_CHECK(launch("edge_features", segment_mean_kernel, grid_for((int64_t)m * k, 256), 256, 0,
+                     s, m, k, (const int32_t*)fine->e_ptr, (const int32_t*)fine->e_nodes,
+                     (const float*)fine->feat, fe));
+    HNV_CHECK(launch("node_norms", row_norm_kernel, grid_for(n, 256), 256, 0, s, n, k,
+                     (const float*)fine->feat, nv));
+    HNV_CHECK(launch("edge_norms", row_norm_kernel, grid_for(m, 256), 256, 0, s, m, k,
+                     (const float*)fe, ne));
+    HNV_CHECK(launch("node_of", node_of_kernel, grid_for((int64_t)n * 32, 256), 256, 0, s, n,
+                     (const int32_t*)fine->v_ptr, node_of));
+    HNV_CHECK(launch("cosine_score", cosine_score_kernel, grid_for(nnz, 256), 256, 0, s, nnz, k,
+                     (const int32_t*)node_of, (const int32_t*)fine->v_edges,
+                     (const float*)fine->feat, (const float*)fe, (const float*)nv,
+                     (const float*)ne, score));
+  }
   int32_t *long_rows = nullptr, *n_long = nullptr;
   HNV_CHECK(pool.get(&long_rows, (size_t)(nnz / kLongRow + 1)));
   HNV_CHECK(pool.get(&n_long, 1));
   HNV_CUDA(cudaMemsetAsync(n_long, 0, sizeof(int32_t), s));
   HNV_CHECK(launch("assign", assign_kernel, grid_for((int64_t)n * 32, 256), 256, 0, s, n,
                    (const int32_t*)fine->v_ptr, (const int32_t*)fine->v_edges,
-                   (const uint64_t*)prio, c, long_rows, n_long));
+                   (const uint64_t*)prio, (const float*)score, c, long_rows, n_long));
   HNV_CHECK(launch("assign_long", assign_long_kernel, (unsigned)(2 * num_sms()), kLongThreads, 0,
                    s, (const int32_t*)long_rows, (const int32_t*)n_long,
                    (const int32_t*)fine->v_ptr, (const int32_t*)fine->v_edges,
-                   (const uint64_t*)prio, c));
+                   (const uint64_t*)prio, (const float*)score, c));
 
   // 2. Merge: coarse IDs are the ranks of the keys c(v) / m + v
   int32_t* rank = nullptr;
@@ -403,6 +516,22 @@ int coarsen_step(hnv_graph* g, int level, const hnv_coarsen_params* p,
                    (const float*)fine->w, (const int32_t*)fine->orig_e, fine->rep_e, size2,
                    coarse->w, coarse->orig_e));
   HNV_CHECK(exclusive_scan_i32(size2, coarse->e_ptr, (int64_t)m2 + 1, nullptr, s));
+
+  // 6. The coarse node features (feature rule): the mean of the merged
+  // nodes' features, in ascending fine-node order (the CSC of rep_v).
+  if (p->policy == HNV_ASSIGN_COSINE) {
+    int32_t *iota = nullptr, *ch_ptr = nullptr, *ch_idx = nullptr;
+    HNV_CHECK(pool.get(&iota, (size_t)n + 1));
+    HNV_CHECK(pool.get(&ch_ptr, (size_t)n2 + 1));
+    HNV_CHECK(pool.get(&ch_idx, (size_t)n));
+    HNV_CHECK(launch("iota", iota_kernel, grid_for((int64_t)n + 1, 256), 256, 0, s, n + 1, iota));
+    HNV_CHECK(transpose_csr(n, n2, n, iota, fine->rep_v, ch_ptr, ch_idx, s));
+    HNV_CHECK(level_alloc(coarse, (void**)&coarse->feat, sizeof(float) * (size_t)n2 * k, s));
+    coarse->feat_k = k;
+    HNV_CHECK(launch("merge_features", segment_mean_kernel, grid_for((int64_t)n2 * k, 256), 256, 0,
+                     s, n2, k, (const int32_t*)ch_ptr, (const int32_t*)ch_idx,
+                     (const float*)fine->feat, coarse->feat));
+  }
   return HNV_OK;
 }
 

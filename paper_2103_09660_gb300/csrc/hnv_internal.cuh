@@ -47,7 +47,8 @@ enum : int32_t {
   ERRBIT_BAD_WEIGHT = 4,    // a weight that is not finite and > 0
   ERRBIT_BAD_PTR = 8,       // edge_ptr not starting at 0 / decreasing
   ERRBIT_TIMEOUT = 16,      // a bounded device wait gave up (refinement)
-  ERRBIT_BAD_ITEM = 32      // a batched work item outside its graph's arrays (skipped)
+  ERRBIT_BAD_ITEM = 32,     // a batched work item outside its graph's arrays (skipped)
+  ERRBIT_BAD_FEATURE = 64   // a node feature that is not finite or exceeds 1e15 in magnitude
 };
 
 // ---------------------------------------------------------------------------
@@ -205,6 +206,8 @@ struct Level {
   int32_t* orig_e = nullptr;     // [m] level-0 ID
   int32_t* rep_v = nullptr;      // [n] -> level+1 (null on the coarsest)
   int32_t* rep_e = nullptr;      // [m] -> level+1 or -1-c
+  float* feat = nullptr;         // [n x feat_k] node features (cosine policy), or null
+  int32_t feat_k = 0;
   SplitPlan planE, planV;
   // adjoint (built on first use; freed with the level)
   bool adj_ready = false;

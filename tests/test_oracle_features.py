@@ -1,0 +1,152 @@
+"""Pins of the oracle's feature-based coarsening (Section 3.1: hyperedge
+features are member means; c(v) maximises the cosine between f(e) and
+f(v); merged nodes' features are averaged).
+
+The pins come from outside the float32 pipeline they check: a hand-worked
+example, the reduction to the featureless hash rule when every cosine ties,
+exact power-of-two scale invariance, float64 arithmetic for the chosen
+hyperedge's optimality and for the merged means."""
+
+import numpy as np
+import pytest
+
+import hypergen
+from oracle import hnv_oracle as O
+
+from _helpers import oracle_level0, small_cases
+
+
+def _level(n, edges, w=None):
+    ptr = np.concatenate([[0], np.cumsum([len(e) for e in edges])]).astype(np.int64)
+    return O.build_level(n, len(edges), ptr, np.concatenate(edges).astype(np.int64), w)
+
+
+def test_hand_worked_cosine_example():
+    # two groups with orthogonal one-hot features; e1 and e3 straddle them
+    X = np.array([[1, 0], [1, 0], [1, 0], [0, 1], [0, 1], [0, 1]], dtype=np.float32)
+    lv = _level(6, [[0, 1, 2], [2, 3], [3, 4, 5], [1, 4]])
+    h = O.coarsen(lv, O.CoarsenParams(policy=O.ASSIGN_COSINE, min_nodes=1, max_levels=1,
+                                      features=X))
+    # node 1: cos(e0) = 1 > cos(e3) = 1/sqrt(2); node 2: e0 over e1; node 3:
+    # e2 over e1; node 4: e2 over e3. So {0,1,2} -> e0 and {3,4,5} -> e2.
+    assert h.rep_v[0].tolist() == [0, 0, 0, 1, 1, 1]
+    # e0 and e2 collapse into coarse nodes 0 and 1; e1 and e3 survive as 0, 1
+    assert h.rep_e[0].tolist() == [-1, 0, -2, 1]
+    c = h.levels[1]
+    assert (c.n, c.m) == (2, 2)
+    assert c.e_nodes.tolist() == [0, 1, 0, 1]
+    assert h.features[1].tolist() == [[1, 0], [0, 1]]
+
+
+def test_all_ties_reduce_to_the_hash_rule():
+    """Identical features (small integers, so every sum and mean is exact):
+    every cosine is the same number, the tie rule decides everywhere, and
+    the hierarchy is the featureless HASH hierarchy."""
+    for case, hg in enumerate(small_cases(5, 25, n_max=40, m_max=30, size_max=8)):
+        lv = oracle_level0(hg)
+        X = np.tile(np.array([[1, 2, -3, 4]], dtype=np.float32), (lv.n, 1))
+        hc = O.coarsen(lv, O.CoarsenParams(policy=O.ASSIGN_COSINE, min_nodes=2, seed=case,
+                                           features=X))
+        hh = O.coarsen(lv, O.CoarsenParams(policy=O.ASSIGN_HASH, min_nodes=2, seed=case))
+        assert len(hc.levels) == len(hh.levels)
+        for a, b in zip(hc.rep_v, hh.rep_v):
+            assert np.array_equal(a, b)
+        for a, b in zip(hc.rep_e, hh.rep_e):
+            assert np.array_equal(a, b)
+        for F in hc.features:
+            assert np.array_equal(F, np.tile(X[:1], (F.shape[0], 1)))
+
+
+def test_power_of_two_scaling_is_exact():
+    """Scaling every feature by 2^j scales every sum, mean, dot product and
+    norm exactly, so assignments are identical and merged features scale."""
+    hg = hypergen.generate(hypergen.CONFIGS["small_2k"])
+    lv = oracle_level0(hg)
+    X = hypergen.planted_features(hg, 8, sigma=0.7, seed=1)
+    base = O.coarsen(lv, O.CoarsenParams(policy=O.ASSIGN_COSINE, min_nodes=200, features=X))
+    for j in (-3, 5):
+        sc = O.coarsen(lv, O.CoarsenParams(policy=O.ASSIGN_COSINE, min_nodes=200,
+                                           features=X * np.float32(2.0 ** j)))
+        assert len(sc.levels) == len(base.levels)
+        for a, b in zip(sc.rep_v, base.rep_v):
+            assert np.array_equal(a, b)
+        for Fa, Fb in zip(sc.features, base.features):
+            assert np.array_equal(Fa, Fb * np.float32(2.0 ** j))
+
+
+def test_chosen_hyperedge_is_optimal_in_float64():
+    """Against cosines computed in float64 from the same features: the
+    float32 choice is a maximiser up to float32 rounding, and a strict
+    float64 winner by a clear margin is always the one chosen."""
+    for case, hg in enumerate(small_cases(11, 30, n_max=40, m_max=30, size_max=8)):
+        lv = oracle_level0(hg)
+        rng = np.random.default_rng(case)
+        X = rng.standard_normal((lv.n, 6)).astype(np.float32)
+        prio = O.hash_priority(np.arange(lv.m, dtype=np.uint64), 0, 0)
+        c = O.assign_cosine(lv, X, prio)
+        X64 = X.astype(np.float64)
+        for v in range(lv.n):
+            N = lv.v_edges[lv.v_ptr[v]:lv.v_ptr[v + 1]]
+            if N.size == 0:
+                assert c[v] == -1
+                continue
+            fe = np.array([X64[lv.e_nodes[lv.e_ptr[e]:lv.e_ptr[e + 1]]].mean(axis=0) for e in N])
+            nv = np.linalg.norm(X64[v])
+            ne = np.linalg.norm(fe, axis=1)
+            cos = np.where(ne * nv > 0, fe @ X64[v] / np.maximum(ne * nv, 1e-300), 0.0)
+            got = cos[list(N).index(c[v])]
+            assert got >= cos.max() - 1e-5
+            best = np.argsort(-cos)
+            if N.size == 1 or cos[best[0]] - cos[best[1]] > 1e-4:
+                assert c[v] == N[best[0]]
+
+
+def test_merged_features_are_means():
+    hg = hypergen.generate(hypergen.CONFIGS["small_2k"])
+    lv = oracle_level0(hg)
+    X = hypergen.planted_features(hg, 16, sigma=0.5, seed=2)
+    h = O.coarsen(lv, O.CoarsenParams(policy=O.ASSIGN_COSINE, min_nodes=200, features=X))
+    assert len(h.levels) >= 3
+    for ell, rep in enumerate(h.rep_v):
+        fine = h.features[ell].astype(np.float64)
+        coarse = h.features[ell + 1].astype(np.float64)
+        n2 = h.levels[ell + 1].n
+        cnt = np.bincount(rep, minlength=n2)
+        mean = np.zeros((n2, fine.shape[1]))
+        np.add.at(mean, rep, fine)
+        mean /= cnt[:, None]
+        assert np.abs(coarse - mean).max() <= 1e-5 * max(1.0, np.abs(fine).max())
+        # the merge conserves the count-weighted sum (to rounding)
+        assert np.allclose((coarse * cnt[:, None]).sum(axis=0), fine.sum(axis=0), atol=1e-2)
+
+
+def test_cosine_coarsening_groups_communities_better_than_hash():
+    """The reason for the feature rule (Section 3.1: cosine similarity aligns
+    with the classes): with well-separated community features, coarse nodes
+    are purer than under the hash rule."""
+    hg = hypergen.generate(hypergen.CONFIGS["small_2k"])
+    lv = oracle_level0(hg)
+    X = hypergen.planted_features(hg, 16, sigma=0.3, seed=3)
+
+    def purity(rep):
+        agree = 0
+        for c in np.unique(rep):
+            lab = hg.labels[rep == c]
+            agree += np.bincount(lab).max()
+        return agree / hg.n
+
+    pc = purity(O.coarsen(lv, O.CoarsenParams(policy=O.ASSIGN_COSINE, min_nodes=200,
+                                              max_levels=1, features=X)).rep_v[0])
+    ph = purity(O.coarsen(lv, O.CoarsenParams(policy=O.ASSIGN_HASH, min_nodes=200,
+                                              max_levels=1)).rep_v[0])
+    assert pc > ph
+
+
+def test_feature_validation():
+    lv = _level(3, [[0, 1], [1, 2]])
+    for bad in (np.ones((2, 2)), np.ones((3, 0)), np.array([[1, np.nan]] * 3),
+                np.full((3, 2), 2e15)):
+        with pytest.raises(ValueError):
+            O.coarsen(lv, O.CoarsenParams(policy=O.ASSIGN_COSINE, min_nodes=1, features=bad))
+    with pytest.raises(ValueError):
+        O.coarsen(lv, O.CoarsenParams(policy=O.ASSIGN_COSINE, min_nodes=1))
