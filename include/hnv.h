@@ -222,6 +222,20 @@ int hnv_refine(hnv_graph* g, int level, void* z_v, void* z_e, hnv_dtype dt, int 
                float omega, int sweeps, hnv_sweep mode, hnv_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * hnv_refine_until -- hnv_refine with the stopping rule the experiments of
+ * Section 4 name as the alternative to a fixed iteration count: stop once
+ * two consecutive iterates differ by at most eps. The difference of a sweep
+ * is the largest |change| of any coordinate of any node or hyperedge row
+ * (as stored). Runs at most max_sweeps sweeps; eps < 0 never stops early.
+ *   sweeps_done [out] : sweeps run; last_delta [out] : the last difference
+ * Synchronises the stream after every sweep (to read the difference) and
+ * allocates two row buffers of the level for the previous iterate.
+ * ------------------------------------------------------------------------- */
+int hnv_refine_until(hnv_graph* g, int level, void* z_v, void* z_e, hnv_dtype dt, int d,
+                     float omega, int max_sweeps, float eps, hnv_sweep mode,
+                     int32_t* sweeps_done, float* last_delta, hnv_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * hnv_vcycle -- the refinement half of the V-cycle (Section 3, Fig. 1):
  * refine the coarsest level L from z_coarsest, then for l = L-1 .. 0
  * project onto level l and refine it; write level 0's result.

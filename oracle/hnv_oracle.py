@@ -559,6 +559,28 @@ def refine(lv: Level, z_v: np.ndarray, z_e: np.ndarray, omega: float,
     return z_v, z_e
 
 
+def refine_until(lv: Level, z_v: np.ndarray, z_e: np.ndarray, omega: float,
+                 max_sweeps: int, eps: float, mode: int = SWEEP_TWO_PHASE):
+    """Refinement with the stopping rule the experiments name as an
+    alternative to a fixed sweep count (Section 4, experimental setup): stop
+    once the difference between two consecutive iterates is at most eps.
+    READING of "difference": the largest absolute change of any coordinate
+    of any node or hyperedge row during one sweep. At most max_sweeps
+    sweeps. Returns (z_v, z_e, sweeps_done, per-sweep differences)."""
+    z_v = np.array(z_v, dtype=np.float64)
+    z_e = np.array(z_e, dtype=np.float64)
+    deltas = []
+    for _ in range(max_sweeps):
+        nv, ne = refine(lv, z_v, z_e, omega, 1, mode)
+        dv = float(np.abs(nv - z_v).max()) if nv.size else 0.0
+        de = float(np.abs(ne - z_e).max()) if ne.size else 0.0
+        z_v, z_e = nv, ne
+        deltas.append(max(dv, de))
+        if deltas[-1] <= eps:
+            break
+    return z_v, z_e, len(deltas), deltas
+
+
 # ---------------------------------------------------------------------------
 # The V-cycle
 # ---------------------------------------------------------------------------

@@ -30,7 +30,7 @@ __all__ = [
     "Graph", "hnv_build_incidence", "hnv_coarsen", "hnv_project", "hnv_refine",
     "hnv_vcycle", "hnv_refine_noalloc", "hnv_set_weights", "hnv_checkpoint_floats",
     "hnv_vcycle_save", "hnv_vcycle_backward", "vcycle_autograd", "Batch", "kernel_launch_count",
-    "hnv_set_node_features", "hnv_copy_level_features", "timing_enable", "timing_reset", "timing_read",
+    "hnv_set_node_features", "hnv_copy_level_features", "hnv_refine_until", "timing_enable", "timing_reset", "timing_read",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -94,6 +94,9 @@ def _declare(L):
         "hnv_graph_free": (None, [_P]),
         "hnv_sync_status": (ctypes.c_int, [_P, _P]),
         "hnv_set_node_features": (ctypes.c_int, [_P, _P, i32, ctypes.c_int, _P]),
+        "hnv_refine_until": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_int,
+                                            f32, ctypes.c_int, f32, ctypes.c_int,
+                                            ctypes.POINTER(i32), ctypes.POINTER(f32), _P]),
         "hnv_copy_level_features": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t,
                                                    ctypes.c_int, _P]),
         "hnv_level_feature_dim": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(i32)]),
@@ -267,6 +270,20 @@ def hnv_refine_noalloc(g: int, level: int, z_v, z_e, omega: float = 0.5, sweeps:
                                     _dev_ptr(z_e, torch.float32, "z_e"), F32, int(d),
                                     float(omega), int(sweeps), _stream_handle(stream)),
            "hnv_refine_noalloc")
+
+
+def hnv_refine_until(g: int, level: int, z_v, z_e, omega: float = 0.5, max_sweeps: int = 80,
+                     eps: float = 1e-4, mode: int = SWEEP_TWO_PHASE, stream=None):
+    """Sweeps until one changes no coordinate by more than eps (or
+    max_sweeps). Returns (sweeps_done, last_difference)."""
+    dt, tdt = _emb_dtype(z_v)
+    d = z_v.shape[1]
+    done, delta = ctypes.c_int32(), ctypes.c_float()
+    _check(lib().hnv_refine_until(g, level, _dev_ptr(z_v, tdt, "z_v"), _dev_ptr(z_e, tdt, "z_e"),
+                                  dt, int(d), float(omega), int(max_sweeps), float(eps), int(mode),
+                                  ctypes.byref(done), ctypes.byref(delta),
+                                  _stream_handle(stream)), "hnv_refine_until")
+    return done.value, delta.value
 
 
 def hnv_vcycle(g: int, z_coarsest, z_v_out, z_e_out, omega: float = 0.5, sweeps: int = 10,
@@ -502,6 +519,11 @@ class Graph:
 
     def refine(self, level: int, z_v, z_e, omega=0.5, sweeps=10, mode=SWEEP_TWO_PHASE):
         hnv_refine(self.handle, level, z_v, z_e, omega, sweeps, mode, self.stream)
+
+    def refine_until(self, level: int, z_v, z_e, omega=0.5, max_sweeps=80, eps=1e-4,
+                     mode=SWEEP_TWO_PHASE):
+        return hnv_refine_until(self.handle, level, z_v, z_e, omega, max_sweeps, eps, mode,
+                                self.stream)
 
     def project(self, fine_level: int, zc_v, zc_e, zf_v, zf_e):
         hnv_project(self.handle, fine_level, zc_v, zc_e, zf_v, zf_e, self.stream)

@@ -473,6 +473,28 @@ int hnv_refine(hnv_graph* g, int level, void* z_v, void* z_e, hnv_dtype dt, int 
                       reinterpret_cast<cudaStream_t>(stream));
 }
 
+int hnv_refine_until(hnv_graph* g, int level, void* z_v, void* z_e, hnv_dtype dt, int d,
+                     float omega, int max_sweeps, float eps, hnv_sweep mode,
+                     int32_t* sweeps_done, float* last_delta, hnv_stream_t stream) {
+  clear_error_detail();
+  if (!g) HNV_FAIL(HNV_ERR_INVALID_ARG, "graph is NULL");
+  if (!sweeps_done || !last_delta) HNV_FAIL(HNV_ERR_INVALID_ARG, "NULL output");
+  if (level < 0 || level >= (int)g->levels.size())
+    HNV_FAIL(HNV_ERR_OUT_OF_RANGE, "level %d not in [0, %d)", level, (int)g->levels.size());
+  HNV_CHECK(check_embedding_args(dt, d));
+  if (!(omega >= 0.f && omega <= 1.f)) HNV_FAIL(HNV_ERR_INVALID_ARG, "omega must be in [0, 1]");
+  if (max_sweeps < 0) HNV_FAIL(HNV_ERR_INVALID_ARG, "max_sweeps < 0");
+  if (eps != eps) HNV_FAIL(HNV_ERR_INVALID_ARG, "eps is NaN");
+  if (mode != HNV_SWEEP_TWO_PHASE && mode != HNV_SWEEP_JACOBI)
+    HNV_FAIL(HNV_ERR_INVALID_ARG, "unknown sweep mode %d", (int)mode);
+  const Level& lv = g->levels[level];
+  HNV_CHECK(check_buf(z_v, lv.n, "z_v"));
+  HNV_CHECK(check_buf(z_e, lv.m, "z_e"));
+  DeviceGuard dgd(g->device);
+  return refine_level_until(g, level, z_v, z_e, (int)dt, d, omega, max_sweeps, eps, (int)mode,
+                            sweeps_done, last_delta, reinterpret_cast<cudaStream_t>(stream));
+}
+
 int hnv_vcycle(hnv_graph* g, const void* z_coarsest, void* z_v_out, void* z_e_out, hnv_dtype dt,
                int d, float omega, int sweeps_per_level, hnv_sweep mode, int buffers_on_device,
                hnv_stream_t stream) {

@@ -285,6 +285,11 @@ int refine_level(hnv_graph* g, int level, void* z_v, void* z_e, int dtype, int d
                  int sweeps, int mode, cudaStream_t s);
 int project_level(const hnv_graph* g, int fine_level, const void* zc_v, const void* zc_e,
                   void* zf_v, void* zf_e, int dtype, int d, cudaStream_t s);
+// Sweeps until the largest change of any coordinate in a sweep is <= eps, or
+// max_sweeps (synchronises after every sweep to read that change).
+int refine_level_until(hnv_graph* g, int level, void* z_v, void* z_e, int dtype, int d,
+                       float omega, int max_sweeps, float eps, int mode, int32_t* sweeps_done,
+                       float* last_delta, cudaStream_t s);
 // adjoint.cu: weights from a level-0 weight vector (device) to every level,
 // and the reverse mode of the two-phase float32 V-cycle.
 int set_weights_impl(hnv_graph* g, const float* d_w0, cudaStream_t s);

@@ -150,3 +150,29 @@ def test_feature_validation():
             O.coarsen(lv, O.CoarsenParams(policy=O.ASSIGN_COSINE, min_nodes=1, features=bad))
     with pytest.raises(ValueError):
         O.coarsen(lv, O.CoarsenParams(policy=O.ASSIGN_COSINE, min_nodes=1))
+
+
+# ---------------------------------------------------------------------------
+# The epsilon stopping rule (Section 4: stop once two consecutive iterates
+# differ by at most eps)
+# ---------------------------------------------------------------------------
+
+def test_refine_until_rules():
+    hg = hypergen.generate(hypergen.CONFIGS["small_2k"])
+    lv = oracle_level0(hg)
+    rng = np.random.default_rng(0)
+    z = rng.standard_normal((lv.n + lv.m, 8))
+    zv, ze = z[:lv.n], z[lv.n:]
+    # eps < 0 never stops early: the same as a fixed sweep count
+    a = O.refine_until(lv, zv, ze, 0.5, 7, -1.0)
+    b = O.refine(lv, zv, ze, 0.5, 7)
+    assert a[2] == 7 and np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    # a constant embedding is a fixed point (Section 3.3 relaxation of a
+    # convex combination): the first sweep changes nothing and stops
+    c = O.refine_until(lv, np.full_like(zv, 2.5), np.full_like(ze, 2.5), 0.5, 9, 0.0)
+    assert c[2] == 1 and c[3] == [0.0]
+    # the differences shrink towards 0 (the sweeps converge to constants per
+    # connected component), so a small eps is reached before many sweeps
+    d = O.refine_until(lv, zv, ze, 0.5, 400, 1e-3)
+    assert d[2] < 400 and d[3][-1] <= 1e-3 < d[3][-2]
+    assert d[3][-1] < d[3][0] / 100
