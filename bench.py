@@ -72,6 +72,31 @@ def max_over_ranks(x: float, ws: int, device=None) -> float:
     return float(t.item())
 
 
+def workload_config(args, spec, hg, ws: int) -> dict:
+    """The workload a line is measured on (the same for both arms)."""
+    return {"workload": args.workload, "n": hg.n, "m": hg.m, "nnz": hg.nnz, "d": spec.d,
+            "sweeps_per_level": spec.sweeps, "omega": 0.5, "sweep": "two_phase",
+            "min_nodes": spec.min_nodes, "max_levels": spec.max_levels,
+            "storage": "bf16 rows, f32 sums" if args.dtype == "bf16" else "f32",
+            "l2": "inputs larger than L2 (node and hyperedge embedding tables)",
+            "parallelism": "replicas" if ws > 1 else "single GPU"}
+
+
+def shard_units(weights, ws: int, rank: int) -> list:
+    """Indices of the units (independent graphs) rank `rank` of `ws` takes:
+    longest-processing-time first, each unit to the rank with the least
+    weight so far (ties to the lower rank). Every rank computes the same
+    assignment; every unit goes to exactly one rank."""
+    load = [0.0] * ws
+    mine = []
+    for i in sorted(range(len(weights)), key=lambda i: (-weights[i], i)):
+        r = min(range(ws), key=lambda q: (load[q], q))
+        load[r] += weights[i]
+        if r == rank:
+            mine.append(i)
+    return sorted(mine)
+
+
 def aggregate(units_per_rank: float, seconds: list) -> float:
     """Whole-job throughput: units of all ranks over the slowest rank."""
     return units_per_rank * len(seconds) / max(seconds)
@@ -406,13 +431,9 @@ def run_ours(args, ws, rank, local):
         "warmup": args.warmup, "ms_per_step": sec_max / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
         "data": "synthetic",
-        "config": {"workload": args.workload, "n": hg.n, "m": hg.m, "nnz": hg.nnz, "d": spec.d,
-                   "sweeps_per_level": spec.sweeps, "omega": 0.5, "sweep": "two_phase",
-                   "levels": len(sizes), "level_sizes": [list(s) for s in sizes],
-                   "updates_per_step": updates,
-                   "storage": "bf16 rows, f32 sums" if args.dtype == "bf16" else "f32",
-                   "l2": "inputs larger than L2 (node and hyperedge embedding tables)",
-                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "config": workload_config(args, spec, hg, ws),
+        "hierarchy": {"levels": len(sizes), "level_sizes": [list(s) for s in sizes],
+                      "updates_per_step": updates},
         "vcycle_ms": sec_max / args.steps * 1e3,
         "phase_ms_per_step": {k: round(v["ms_per_step"], 3) for k, v in phases.items()},
         "refine_only_updates_per_s": updates / ((phases["refine_e"]["ms_per_step"] +
@@ -452,7 +473,7 @@ def run_reference(args, ws, rank, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_t / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": args.workload, "n": hg.n, "m": hg.m, "nnz": hg.nnz, "d": spec.d},
+        "config": workload_config(args, spec, hg, ws),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
                          "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -704,16 +725,26 @@ def run_batch_study(args):
     BF16) against the batched path (BF16 and FP32; direct launches, one
     captured CUDA graph, autotuned row classes). Device-resident buffers,
     CUDA-event timing on one stream; all variants give the same rows per
-    dtype (tests/test_gpu_batch.py checks that)."""
+    dtype (tests/test_gpu_batch.py checks that).
+
+    Under torchrun the graphs are independent units: each rank takes its
+    share (shard_units, balanced by node count), no data moves between
+    ranks, and every time is the slowest rank's; throughput counts the
+    updates of all ranks."""
     import torch
     import paper_2103_09660_gb300 as H
     from paper_2103_09660_gb300 import build as B
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        init_dist(ws, "nccl")
     B.build()
-    specs = hypergen.batch_specs(args.batch_count)
+    all_specs = hypergen.batch_specs(args.batch_count)
+    specs = [all_specs[i] for i in shard_units([sp.n for sp in all_specs], ws, rank)]
     t0 = time.time()
     hgs = [hypergen.generate(sp) for sp in specs]
     t_gen = time.time() - t0
-    dev = torch.device("cuda", 0)
+    dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     Gs = []
     t0 = time.time()
@@ -748,12 +779,20 @@ def run_batch_study(args):
         zc, zv, ze = bufs[name]
         return lambda: bat.vcycle(zc, zv, ze, om, k, use_cuda_graph=graph)
 
+    total_updates = updates
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([float(updates)], dtype=torch.float64, device=dev)
+        dist.all_reduce(t)
+        total_updates = float(t.item())
+
     def timed(fn):
         for _ in range(max(args.warmup, 1)):
             fn()
         torch.cuda.synchronize()
         ts = []
         for _ in range(args.steps):
+            barrier(ws)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             l0 = H.kernel_launch_count()
@@ -761,8 +800,9 @@ def run_batch_study(args):
             e1.record(stream)
             torch.cuda.synchronize()
             ts.append(e0.elapsed_time(e1))
-        return {"ms": float(np.median(ts)), "updates_per_s": updates / (np.median(ts) / 1e3),
-                "launches": int(H.kernel_launch_count() - l0)}
+        ms = max_over_ranks(float(np.median(ts)), ws, dev)
+        return {"ms": ms, "updates_per_s": total_updates / (ms / 1e3),
+                "launches_rank0": int(H.kernel_launch_count() - l0)}
 
     res = {}
     res["loop_f32"] = timed(lambda: loop("f32"))
@@ -783,12 +823,16 @@ def run_batch_study(args):
     bat.close()
     for G in Gs:
         G.close()
+    if rank != 0:
+        return
     print(json.dumps({
-        "study": "batched V-cycle vs looping the single-graph path",
-        "graphs": len(Gs), "nodes": int(vo[-1]), "hyperedges": int(eo[-1]),
-        "incidences": int(sum(h.nnz for h in hgs)), "d": d, "sweeps_per_level": k,
+        "study": "batched V-cycle vs looping the single-graph path", "n_gpus": ws,
+        "scaling": "weak" if ws > 1 else None,
+        "graphs_rank0": len(Gs), "graphs": len(all_specs), "nodes_rank0": int(vo[-1]),
+        "hyperedges_rank0": int(eo[-1]), "updates_per_vcycle_all_ranks": total_updates,
+        "incidences_rank0": int(sum(h.nnz for h in hgs)), "d": d, "sweeps_per_level": k,
         "levels_min": min(levels), "levels_max": max(levels),
-        "updates_per_vcycle": updates, "results": res,
+        "updates_per_vcycle_rank0": updates, "results": res,
         "speedup_batched_bf16_tuned_vs_loop_f32":
             res["loop_f32"]["ms"] / res["batched_bf16_graph_tuned"]["ms"],
         "tuning_bf16": tune, "tuning_f32": tune32, "autotune_s": t_tune,
