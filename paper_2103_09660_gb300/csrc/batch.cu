@@ -530,7 +530,7 @@ int build_steps(hnv_batch* b, int dt, int d, const uint8_t* zc, uint8_t* zv0, ui
 
 // lanes per row of class c (0: A, 1: B, 2: rest) for rows of dv vectors
 int class_lanes(const hnv_batch* b, int c, int dv) {
-  const int natural[3] = {8, 16, 32};
+  const int natural[3] = {16, 16, 32};   // the single-graph defaults
   int g = b->lanes[c] > 0 ? b->lanes[c] : natural[c];
   g = std::min(g, next_pow2(dv));
   g = std::max(g, next_pow2((dv + 7) / 8));

@@ -241,72 +241,6 @@ __global__ void pack_image_keys(int32_t m, const int32_t* __restrict__ e_ptr,
   }
 }
 
-// Segmented sort of the image keys: the keys were packed hyperedge by
-// hyperedge, so sorting every hyperedge's segment [e_ptr[e], e_ptr[e+1]) by
-// its low word gives the array a full sort by (e, rep) would. Segments of
-// at most 32 keys: a warp each, bitonic network over the lanes. Up to
-// kSegMax: a block each, bitonic network in shared memory. Longer segments
-// exist only if the level has hyperedges that long; the caller then sorts
-// the whole array instead.
-constexpr int32_t kSegMax = 4096;
-constexpr int kSegThreads = 512;
-
-__global__ void seg_sort_warp(int32_t m, const int32_t* __restrict__ e_ptr,
-                              uint64_t* __restrict__ keys) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); e < m;
-       e += warps) {
-    const int32_t b = e_ptr[e], len = e_ptr[e + 1] - b;
-    if (len < 2 || len > 32) continue;
-    uint32_t x = lane < len ? (uint32_t)keys[b + lane] : 0xffffffffu;
-#pragma unroll
-    for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-      for (int j = k >> 1; j > 0; j >>= 1) {
-        const uint32_t o = __shfl_xor_sync(FULL, x, j);
-        const bool ascending = (lane & k) == 0;
-        const bool lower = (lane & j) == 0;
-        x = (lower == ascending) ? min(x, o) : max(x, o);
-      }
-    }
-    if (lane < len) keys[b + lane] = ((uint64_t)(uint32_t)e << 32) | x;
-  }
-}
-
-__global__ void __launch_bounds__(kSegThreads)
-seg_sort_block(int32_t m, const int32_t* __restrict__ e_ptr, uint64_t* __restrict__ keys) {
-  __shared__ uint32_t sk[kSegMax];
-  for (int64_t e = blockIdx.x; e < m; e += gridDim.x) {
-    const int32_t b = e_ptr[e], len = e_ptr[e + 1] - b;
-    if (len <= 32 || len > kSegMax) continue;
-    int32_t n2 = 64;
-    while (n2 < len) n2 <<= 1;
-    for (int32_t i = threadIdx.x; i < n2; i += kSegThreads)
-      sk[i] = i < len ? (uint32_t)keys[b + i] : 0xffffffffu;
-    __syncthreads();
-    for (int32_t k = 2; k <= n2; k <<= 1) {
-      for (int32_t j = k >> 1; j > 0; j >>= 1) {
-        for (int32_t i = threadIdx.x; i < n2; i += kSegThreads) {
-          const int32_t p = i ^ j;
-          if (p > i) {
-            const uint32_t a = sk[i], c = sk[p];
-            const bool ascending = (i & k) == 0;
-            if ((a > c) == ascending) {
-              sk[i] = c;
-              sk[p] = a;
-            }
-          }
-        }
-        __syncthreads();
-      }
-    }
-    for (int32_t i = threadIdx.x; i < len; i += kSegThreads)
-      keys[b + i] = ((uint64_t)(uint32_t)e << 32) | sk[i];
-    __syncthreads();
-  }
-}
-
 __global__ void max_row_len(int32_t rows, const int32_t* __restrict__ ptr, int32_t* __restrict__ out) {
   int32_t mx = 0;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows;
@@ -459,12 +393,10 @@ int coarsen_step(hnv_graph* g, int level, const hnv_coarsen_params* p,
   HNV_CHECK(launch("pack_image_keys", pack_image_keys, grid_for((int64_t)m * 32, 256), 256, 0, s,
                    m, (const int32_t*)fine->e_ptr, (const int32_t*)fine->e_nodes,
                    (const int32_t*)fine->rep_v, k0));
-  if (max_e_len <= kSegMax) {
-    HNV_CHECK(launch("seg_sort_warp", seg_sort_warp, grid_for((int64_t)m * 32, 256), 256, 0, s, m,
-                     (const int32_t*)fine->e_ptr, k0));
-    if (max_e_len > 32)
-      HNV_CHECK(launch("seg_sort_block", seg_sort_block, (unsigned)(4 * num_sms()), kSegThreads, 0,
-                       s, m, (const int32_t*)fine->e_ptr, k0));
+  // the keys were packed hyperedge by hyperedge: sorting every hyperedge's
+  // run by its low word gives what a full sort by (e, rep) would
+  if (max_e_len <= kSegSortMax) {
+    HNV_CHECK(segmented_sort_low32(m, fine->e_ptr, (const int64_t*)nullptr, max_e_len, k0, s));
     sorted = k0;
   } else {
     int shifts[16];

@@ -148,6 +148,14 @@ int radix_shifts(int low_bits, int high_bits, int* shifts);
 // Number of bits needed to hold values in [0, count).
 int bits_for_count(int64_t count);
 
+// Sorts keys[ptr[i] .. ptr[i+1]) of every segment i < segs by their low 32
+// bits (stable is irrelevant: keys within a segment share their high word).
+// ptr is int32 (ptr32) or int64 (ptr64, when ptr32 is null); max_len bounds
+// the segment lengths and must be <= kSegSortMax.
+constexpr int32_t kSegSortMax = 8192;
+int segmented_sort_low32(int32_t segs, const int32_t* ptr32, const int64_t* ptr64,
+                         int32_t max_len, uint64_t* keys, cudaStream_t s);
+
 int fill_i32(int32_t* p, int32_t value, int64_t n, cudaStream_t s);
 
 // CSC (transpose) of a CSR with ascending rows: col_ptr[n_cols+1] and

@@ -26,6 +26,19 @@ __global__ void check_ptr_kernel(int32_t m, const int64_t* __restrict__ ptr,
   }
 }
 
+// Largest edge_ptr[e+1] - edge_ptr[e] (clamped to 2^30), for choosing the sort.
+__global__ void max_len_i64_kernel(int32_t m, const int64_t* __restrict__ ptr,
+                                   int32_t* __restrict__ out) {
+  int32_t mx = 0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t d = ptr[e + 1] - ptr[e];
+    mx = max(mx, (int32_t)(d < ((int64_t)1 << 30) ? d : ((int64_t)1 << 30)));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx) atomicMax(out, mx);
+}
+
 __global__ void check_weights_kernel(int32_t m, const float* __restrict__ w,
                                      int32_t* __restrict__ err) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
@@ -628,9 +641,21 @@ int build_level0(hnv_graph* g, int32_t n, int32_t m, const int64_t* d_edge_ptr,
                    m, n, d_edge_ptr, d_edge_nodes, k0, g->d_err));
   HNV_CHECK(read_and_clear_err(g, s, &bits));
   if (bits & ERRBIT_NODE_RANGE) HNV_FAIL(HNV_ERR_OUT_OF_RANGE, "a node ID is outside [0, n)");
-  int shifts[16];
-  const int np = radix_shifts(bits_for_count(n), bits_for_count(m), shifts);
-  HNV_CHECK(radix_sort_u64(k0, k1, nnz_in, shifts, np, s, &sorted));
+  // the keys are grouped by hyperedge already: sorting every hyperedge's run
+  // by node gives what a full sort by (e, node) would
+  int32_t max_len = 0;
+  HNV_CUDA(cudaMemsetAsync(g->d_buf + 40, 0, sizeof(int32_t), s));
+  HNV_CHECK(launch("max_len", max_len_i64_kernel, grid_for(m, 256), 256, 0, s, m, d_edge_ptr,
+                   g->d_buf + 40));
+  HNV_CHECK(read_ints(g, g->d_buf + 40, 1, &max_len, s));
+  if (max_len <= kSegSortMax) {
+    HNV_CHECK(segmented_sort_low32(m, nullptr, d_edge_ptr, max_len, k0, s));
+    sorted = k0;
+  } else {
+    int shifts[16];
+    const int np = radix_shifts(bits_for_count(n), bits_for_count(m), shifts);
+    HNV_CHECK(radix_sort_u64(k0, k1, nnz_in, shifts, np, s, &sorted));
+  }
   HNV_CHECK(pool.get(&first, (size_t)nnz_in));
   HNV_CHECK(pool.get(&pos, (size_t)nnz_in));
   HNV_CHECK(pool.get(&cnt, (size_t)m + 1));

@@ -204,7 +204,135 @@ __global__ void low_words(const uint64_t* __restrict__ keys, int64_t n, int32_t*
     out[i] = (int32_t)(uint32_t)keys[i];
 }
 
+// Segmented sort by the low 32 bits of 64-bit keys whose high words are the
+// segment index. Segments of at most 256 keys: a warp each, a bitonic
+// network over 32 lanes x K registers (element i = register i / 32, lane
+// i % 32). Up to kSegSortMax: a block each, a bitonic network in shared
+// memory.
+constexpr int kSegThreads = 512;
+
+template <int K>
+__device__ __forceinline__ void warp_bitonic(uint32_t (&x)[K], int lane) {
+  constexpr int N = 32 * K;
+#pragma unroll
+  for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j >= 32) {
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+          const int rr = r ^ (j >> 5);
+          if (rr > r) {
+            const bool ascending = ((r * 32 + lane) & k) == 0;
+            const uint32_t a = x[r], b = x[rr];
+            const bool swap = (a > b) == ascending;
+            x[r] = swap ? b : a;
+            x[rr] = swap ? a : b;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+          const uint32_t o = __shfl_xor_sync(FULL, x[r], j);
+          const bool ascending = ((r * 32 + lane) & k) == 0;
+          const bool lower = (lane & j) == 0;
+          x[r] = (lower == ascending) ? min(x[r], o) : max(x[r], o);
+        }
+      }
+    }
+  }
+}
+
+template <int K>
+__device__ __forceinline__ void warp_sort_segment(uint64_t* keys, int64_t b, int32_t len,
+                                                  uint32_t e, int lane) {
+  uint32_t x[K];
+#pragma unroll
+  for (int r = 0; r < K; ++r) {
+    const int i = r * 32 + lane;
+    x[r] = i < len ? (uint32_t)keys[b + i] : 0xffffffffu;
+  }
+  warp_bitonic<K>(x, lane);
+#pragma unroll
+  for (int r = 0; r < K; ++r) {
+    const int i = r * 32 + lane;
+    if (i < len) keys[b + i] = ((uint64_t)e << 32) | x[r];
+  }
+}
+
+template <typename P>
+__global__ void seg_sort_warp(int32_t m, const P* __restrict__ e_ptr,
+                              uint64_t* __restrict__ keys) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); e < m;
+       e += warps) {
+    const int64_t b = e_ptr[e];
+    const int32_t len = (int32_t)(e_ptr[e + 1] - b);
+    if (len < 2 || len > 256) continue;      // warp-uniform
+    if (len <= 32) warp_sort_segment<1>(keys, b, len, (uint32_t)e, lane);
+    else if (len <= 64) warp_sort_segment<2>(keys, b, len, (uint32_t)e, lane);
+    else if (len <= 128) warp_sort_segment<4>(keys, b, len, (uint32_t)e, lane);
+    else warp_sort_segment<8>(keys, b, len, (uint32_t)e, lane);
+  }
+}
+
+template <typename P>
+__global__ void __launch_bounds__(kSegThreads)
+seg_sort_block(int32_t m, const P* __restrict__ e_ptr, uint64_t* __restrict__ keys) {
+  __shared__ uint32_t sk[kSegSortMax];
+  for (int64_t e = blockIdx.x; e < m; e += gridDim.x) {
+    const int64_t b = e_ptr[e];
+    const int32_t len = (int32_t)(e_ptr[e + 1] - b);
+    if (len <= 256 || len > kSegSortMax) continue;   // block-uniform
+    int32_t n2 = 512;
+    while (n2 < len) n2 <<= 1;
+    for (int32_t i = threadIdx.x; i < n2; i += kSegThreads)
+      sk[i] = i < len ? (uint32_t)keys[b + i] : 0xffffffffu;
+    __syncthreads();
+    for (int32_t k = 2; k <= n2; k <<= 1) {
+      for (int32_t j = k >> 1; j > 0; j >>= 1) {
+        // pair t: positions i = (t / j) * 2j + t % j and i + j
+        for (int32_t t = threadIdx.x; t < (n2 >> 1); t += kSegThreads) {
+          const int32_t i = (t / j) * (2 * j) + (t % j);
+          const int32_t p = i + j;
+          const uint32_t a = sk[i], c = sk[p];
+          const bool ascending = (i & k) == 0;
+          if ((a > c) == ascending) {
+            sk[i] = c;
+            sk[p] = a;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (int32_t i = threadIdx.x; i < len; i += kSegThreads)
+      keys[b + i] = ((uint64_t)(uint32_t)e << 32) | sk[i];
+    __syncthreads();
+  }
+}
+
 }  // namespace
+
+int segmented_sort_low32(int32_t segs, const int32_t* ptr32, const int64_t* ptr64,
+                         int32_t max_len, uint64_t* keys, cudaStream_t s) {
+  if (max_len > kSegSortMax) HNV_FAIL(HNV_ERR_INVALID_ARG, "segment of %d keys", max_len);
+  if (segs <= 0 || max_len < 2) return HNV_OK;
+  const unsigned gw = grid_for((int64_t)segs * 32, 256);
+  const unsigned gb = (unsigned)(4 * num_sms());
+  if (ptr32) {
+    HNV_CHECK(launch("seg_sort_warp", seg_sort_warp<int32_t>, gw, 256, 0, s, segs, ptr32, keys));
+    if (max_len > 256)
+      HNV_CHECK(launch("seg_sort_block", seg_sort_block<int32_t>, gb, kSegThreads, 0, s, segs,
+                       ptr32, keys));
+  } else {
+    HNV_CHECK(launch("seg_sort_warp", seg_sort_warp<int64_t>, gw, 256, 0, s, segs, ptr64, keys));
+    if (max_len > 256)
+      HNV_CHECK(launch("seg_sort_block", seg_sort_block<int64_t>, gb, kSegThreads, 0, s, segs,
+                       ptr64, keys));
+  }
+  return HNV_OK;
+}
 
 int exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, int32_t* total,
                        cudaStream_t s) {
