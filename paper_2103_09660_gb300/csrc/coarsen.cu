@@ -396,7 +396,7 @@ int coarsen_step(hnv_graph* g, int level, const hnv_coarsen_params* p,
   // the keys were packed hyperedge by hyperedge: sorting every hyperedge's
   // run by its low word gives what a full sort by (e, rep) would
   if (max_e_len <= kSegSortMax) {
-    HNV_CHECK(segmented_sort_low32(m, fine->e_ptr, (const int64_t*)nullptr, max_e_len, k0, s));
+    HNV_CHECK(segmented_sort_low32(m, fine->e_ptr, (const int64_t*)nullptr, max_e_len, nnz, k0, s));
     sorted = k0;
   } else {
     int shifts[16];

@@ -154,7 +154,7 @@ int bits_for_count(int64_t count);
 // the segment lengths and must be <= kSegSortMax.
 constexpr int32_t kSegSortMax = 8192;
 int segmented_sort_low32(int32_t segs, const int32_t* ptr32, const int64_t* ptr64,
-                         int32_t max_len, uint64_t* keys, cudaStream_t s);
+                         int32_t max_len, int64_t total_keys, uint64_t* keys, cudaStream_t s);
 
 int fill_i32(int32_t* p, int32_t value, int64_t n, cudaStream_t s);
 

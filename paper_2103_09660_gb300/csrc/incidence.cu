@@ -383,30 +383,33 @@ __global__ void long_rows_list(const int4* __restrict__ d_items, int32_t n_d,
   if ((threadIdx.x & 31) == 0 && acc) atomicAdd(total, acc);
 }
 
-// Per listed row i: work items per panel (items_pr[p * R + i]), partial
-// slots (row_chunks[i], 0 for a row left whole) and whether it is split
-// into at most mid_chunks pieces (flags[i]) or more (flags[R + i]).
+// Per listed row i (a warp each; lane p < P owns panel p, P <= 32): work
+// items per panel (items_pr[p * R + i]), partial slots (row_chunks[i], 0
+// for a row left whole) and whether it is split into at most mid_chunks
+// pieces (flags[i]) or more (flags[R + i]).
 __global__ void panel_rows(int32_t R, const int32_t* __restrict__ list,
                            const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
                            int32_t cols, int32_t P, int32_t T, int32_t mid_chunks,
                            int32_t* __restrict__ items_pr, int32_t* __restrict__ row_chunks,
                            int32_t* __restrict__ flags) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < R;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < R;
+       i += warps) {
     const int32_t r = list[i];
     const int32_t beg = ptr[r], end = ptr[r + 1];
-    int32_t c = 0, lo = beg;
-    for (int32_t p = 0; p < P; ++p) {
-      const int32_t hi = panel_cut(idx, beg, end, cols, P, p + 1);
-      const int32_t cp = (hi - lo + T - 1) / T;
-      items_pr[(int64_t)p * R + i] = cp;
-      c += cp;
-      lo = hi;
+    const int32_t hi = lane < P ? panel_cut(idx, beg, end, cols, P, lane + 1) : end;
+    int32_t lo = __shfl_up_sync(0xffffffffu, hi, 1);
+    if (lane == 0) lo = beg;
+    const int32_t cp = lane < P ? (hi - lo + T - 1) / T : 0;
+    const int32_t c = __reduce_add_sync(0xffffffffu, cp);
+    if (lane < P) items_pr[(int64_t)lane * R + i] = cp;
+    if (lane == 0) {
+      const bool split = c > 1;
+      row_chunks[i] = split ? c : 0;
+      flags[i] = (split && c <= mid_chunks) ? 1 : 0;
+      flags[(int64_t)R + i] = (split && c > mid_chunks) ? 1 : 0;
     }
-    const bool split = c > 1;
-    row_chunks[i] = split ? c : 0;
-    flags[i] = (split && c <= mid_chunks) ? 1 : 0;
-    flags[(int64_t)R + i] = (split && c > mid_chunks) ? 1 : 0;
   }
 }
 
@@ -416,34 +419,36 @@ __global__ void panel_fill(int32_t R, const int32_t* __restrict__ list,
                            const int32_t* __restrict__ item_off, const int32_t* __restrict__ slot_off,
                            const int32_t* __restrict__ flag_off, int4* __restrict__ items,
                            int4* __restrict__ long_desc) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < R;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < R;
+       i += warps) {
     const int32_t r = list[i];
     const int32_t beg = ptr[r], end = ptr[r + 1];
-    int32_t c = 0;
-    {
-      int32_t lo = beg;
-      for (int32_t p = 0; p < P; ++p) {
-        const int32_t hi = panel_cut(idx, beg, end, cols, P, p + 1);
-        c += (hi - lo + T - 1) / T;
-        lo = hi;
-      }
+    const int32_t hi = lane < P ? panel_cut(idx, beg, end, cols, P, lane + 1) : end;
+    int32_t lo = __shfl_up_sync(0xffffffffu, hi, 1);
+    if (lane == 0) lo = beg;
+    const int32_t cp = lane < P ? (hi - lo + T - 1) / T : 0;
+    // pieces of the panels before this lane's (an inclusive scan, minus its own)
+    int32_t pre = cp;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t t = __shfl_up_sync(0xffffffffu, pre, o);
+      if (lane >= o) pre += t;
     }
+    const int32_t c = __shfl_sync(0xffffffffu, pre, 31);
+    pre -= cp;
     const bool split = c > 1;
-    int32_t slot = split ? slot_off[i] : -1;
-    int32_t lo = beg;
-    for (int32_t p = 0; p < P; ++p) {
-      const int32_t hi = panel_cut(idx, beg, end, cols, P, p + 1);
-      int64_t at = item_off[(int64_t)p * R + i];
+    if (lane < P && cp > 0) {
+      int64_t at = item_off[(int64_t)lane * R + i];
+      int32_t slot = split ? slot_off[i] + pre : -1;
       for (int32_t s0 = lo; s0 < hi; s0 += T) {
         items[at++] = make_int4(r, s0, min(T, hi - s0), slot);
         if (split) ++slot;
       }
-      lo = hi;
     }
-    if (split) {
-      const bool mid = flag_off[i + 1] != flag_off[i];
+    if (lane == 0 && split) {
       // mid rows first, then the rest (flag_off[R + i] counts every mid row)
+      const bool mid = flag_off[i + 1] != flag_off[i];
       const int64_t pos = mid ? (int64_t)flag_off[i] : (int64_t)flag_off[(int64_t)R + i];
       long_desc[pos] = make_int4(r, slot_off[i], c, 0);
     }
@@ -460,7 +465,7 @@ int forced_panels() {
   static int forced = -2;
   if (forced == -2) {
     const char* e = getenv("HNV_PANELS");
-    forced = (e && atoi(e) >= 1) ? std::min(atoi(e), 64) : -1;
+    forced = (e && atoi(e) >= 1) ? std::min(atoi(e), 32) : -1;   // a lane per panel
   }
   return forced;
 }
@@ -508,7 +513,7 @@ int build_panel_plan(hnv_graph* g, std::vector<void*>* owned, const SplitPlan& b
   HNV_CHECK(pool.get(&items_pr, (size_t)npr));
   HNV_CHECK(pool.get(&row_chunks, (size_t)R));
   HNV_CHECK(pool.get(&flags, 2 * (size_t)R + 1));
-  HNV_CHECK(launch("panel_rows", panel_rows, grid_for(R, 256), 256, 0, s, R, (const int32_t*)list,
+  HNV_CHECK(launch("panel_rows", panel_rows, grid_for((int64_t)R * 32, 256), 256, 0, s, R, (const int32_t*)list,
                    ptr, idx, cols, P, T, kMidChunks, items_pr, row_chunks, flags));
   // each array becomes its exclusive prefix sums in place; totals to d_buf
   HNV_CHECK(exclusive_scan_i32(items_pr, items_pr, npr, cnt + 0, s));
@@ -537,7 +542,7 @@ int build_panel_plan(hnv_graph* g, std::vector<void*>* owned, const SplitPlan& b
                              cudaMemcpyDeviceToDevice, s));
   if (n_split > 0)
     HNV_CHECK(owned_alloc(owned, (void**)&plan->long_desc, sizeof(int4) * (size_t)n_split, s));
-  HNV_CHECK(launch("panel_fill", panel_fill, grid_for(R, 256), 256, 0, s, R, (const int32_t*)list,
+  HNV_CHECK(launch("panel_fill", panel_fill, grid_for((int64_t)R * 32, 256), 256, 0, s, R, (const int32_t*)list,
                    ptr, idx, cols, P, T, (const int32_t*)items_pr, (const int32_t*)row_chunks,
                    (const int32_t*)flags, plan->items + n_short, plan->long_desc));
   *panels = P;
@@ -649,7 +654,7 @@ int build_level0(hnv_graph* g, int32_t n, int32_t m, const int64_t* d_edge_ptr,
                    g->d_buf + 40));
   HNV_CHECK(read_ints(g, g->d_buf + 40, 1, &max_len, s));
   if (max_len <= kSegSortMax) {
-    HNV_CHECK(segmented_sort_low32(m, nullptr, d_edge_ptr, max_len, k0, s));
+    HNV_CHECK(segmented_sort_low32(m, nullptr, d_edge_ptr, max_len, nnz_in, k0, s));
     sorted = k0;
   } else {
     int shifts[16];

@@ -260,16 +260,22 @@ __device__ __forceinline__ void warp_sort_segment(uint64_t* keys, int64_t b, int
   }
 }
 
+// Segments longer than 256 are appended to `long_segs` for seg_sort_block.
 template <typename P>
 __global__ void seg_sort_warp(int32_t m, const P* __restrict__ e_ptr,
-                              uint64_t* __restrict__ keys) {
+                              uint64_t* __restrict__ keys, int32_t* __restrict__ long_segs,
+                              int32_t* __restrict__ n_long) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); e < m;
        e += warps) {
     const int64_t b = e_ptr[e];
     const int32_t len = (int32_t)(e_ptr[e + 1] - b);
-    if (len < 2 || len > 256) continue;      // warp-uniform
+    if (len > 256) {                         // warp-uniform
+      if (lane == 0) long_segs[atomicAdd(n_long, 1)] = (int32_t)e;
+      continue;
+    }
+    if (len < 2) continue;
     if (len <= 32) warp_sort_segment<1>(keys, b, len, (uint32_t)e, lane);
     else if (len <= 64) warp_sort_segment<2>(keys, b, len, (uint32_t)e, lane);
     else if (len <= 128) warp_sort_segment<4>(keys, b, len, (uint32_t)e, lane);
@@ -277,14 +283,18 @@ __global__ void seg_sort_warp(int32_t m, const P* __restrict__ e_ptr,
   }
 }
 
+// The listed segments (257 .. kSegSortMax keys), one block each.
 template <typename P>
 __global__ void __launch_bounds__(kSegThreads)
-seg_sort_block(int32_t m, const P* __restrict__ e_ptr, uint64_t* __restrict__ keys) {
+seg_sort_block(const int32_t* __restrict__ long_segs, const int32_t* __restrict__ n_long,
+               const P* __restrict__ e_ptr, uint64_t* __restrict__ keys) {
   __shared__ uint32_t sk[kSegSortMax];
-  for (int64_t e = blockIdx.x; e < m; e += gridDim.x) {
+  const int32_t count = *n_long;
+  for (int32_t q = blockIdx.x; q < count; q += gridDim.x) {
+    const int32_t e = long_segs[q];
     const int64_t b = e_ptr[e];
     const int32_t len = (int32_t)(e_ptr[e + 1] - b);
-    if (len <= 256 || len > kSegSortMax) continue;   // block-uniform
+    if (len > kSegSortMax) continue;         // block-uniform (the caller rules it out)
     int32_t n2 = 512;
     while (n2 < len) n2 <<= 1;
     for (int32_t i = threadIdx.x; i < n2; i += kSegThreads)
@@ -315,21 +325,28 @@ seg_sort_block(int32_t m, const P* __restrict__ e_ptr, uint64_t* __restrict__ ke
 }  // namespace
 
 int segmented_sort_low32(int32_t segs, const int32_t* ptr32, const int64_t* ptr64,
-                         int32_t max_len, uint64_t* keys, cudaStream_t s) {
+                         int32_t max_len, int64_t total_keys, uint64_t* keys, cudaStream_t s) {
   if (max_len > kSegSortMax) HNV_FAIL(HNV_ERR_INVALID_ARG, "segment of %d keys", max_len);
   if (segs <= 0 || max_len < 2) return HNV_OK;
+  TempPool pool(s);
+  int32_t *long_segs = nullptr, *n_long = nullptr;
+  HNV_CHECK(pool.get(&long_segs, (size_t)(total_keys / 257 + 1)));
+  HNV_CHECK(pool.get(&n_long, 1));
+  HNV_CUDA(cudaMemsetAsync(n_long, 0, sizeof(int32_t), s));
   const unsigned gw = grid_for((int64_t)segs * 32, 256);
   const unsigned gb = (unsigned)(4 * num_sms());
   if (ptr32) {
-    HNV_CHECK(launch("seg_sort_warp", seg_sort_warp<int32_t>, gw, 256, 0, s, segs, ptr32, keys));
+    HNV_CHECK(launch("seg_sort_warp", seg_sort_warp<int32_t>, gw, 256, 0, s, segs, ptr32, keys,
+                     long_segs, n_long));
     if (max_len > 256)
-      HNV_CHECK(launch("seg_sort_block", seg_sort_block<int32_t>, gb, kSegThreads, 0, s, segs,
-                       ptr32, keys));
+      HNV_CHECK(launch("seg_sort_block", seg_sort_block<int32_t>, gb, kSegThreads, 0, s,
+                       (const int32_t*)long_segs, (const int32_t*)n_long, ptr32, keys));
   } else {
-    HNV_CHECK(launch("seg_sort_warp", seg_sort_warp<int64_t>, gw, 256, 0, s, segs, ptr64, keys));
+    HNV_CHECK(launch("seg_sort_warp", seg_sort_warp<int64_t>, gw, 256, 0, s, segs, ptr64, keys,
+                     long_segs, n_long));
     if (max_len > 256)
-      HNV_CHECK(launch("seg_sort_block", seg_sort_block<int64_t>, gb, kSegThreads, 0, s, segs,
-                       ptr64, keys));
+      HNV_CHECK(launch("seg_sort_block", seg_sort_block<int64_t>, gb, kSegThreads, 0, s,
+                       (const int32_t*)long_segs, (const int32_t*)n_long, ptr64, keys));
   }
   return HNV_OK;
 }
