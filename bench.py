@@ -78,7 +78,10 @@ def workload_config(args, spec, hg, ws: int) -> dict:
             "sweeps_per_level": spec.sweeps, "omega": 0.5, "sweep": "two_phase",
             "min_nodes": spec.min_nodes, "max_levels": spec.max_levels,
             "storage": "bf16 rows, f32 sums" if args.dtype == "bf16" else "f32",
-            "l2": "inputs larger than L2 (node and hyperedge embedding tables)",
+            "l2": ("inputs larger than L2 (node and hyperedge embedding tables)"
+                   if max(hg.n, hg.m) * spec.d * 4 > 129e6 else
+                   "tables fit in L2; no flush between steps (the incidence build and "
+                   "coarsening of each step rewrite every array)"),
             "parallelism": "replicas" if ws > 1 else "single GPU"}
 
 

@@ -116,3 +116,50 @@ def test_batch_rejects_bad_arguments(H):
         assert ei.value.code == -7
     for G in Gs:
         G.close()
+
+
+def _hub_graph(n, hub_edges, seed):
+    """A hypergraph whose node 0 is in `hub_edges` hyperedges (a split row of
+    many chunks on the node side), plus random small hyperedges."""
+    rng = np.random.default_rng(seed)
+    edges = [[0, 1 + (i % (n - 2)), 2 + (i % (n - 2))] for i in range(hub_edges)]
+    edges += [sorted(rng.choice(np.arange(1, n), 3, replace=False).tolist()) for _ in range(n)]
+    ptr = np.concatenate([[0], np.cumsum([len(e) for e in edges])]).astype(np.int64)
+    return hypergen.Hypergraph(n=n, m=len(edges), edge_ptr=ptr,
+                               edge_nodes=np.concatenate(edges).astype(np.int32),
+                               weights=rng.uniform(0.5, 2.0, len(edges)).astype(np.float32))
+
+
+@pytest.mark.parametrize("dtname,d", [("bf16", 8), ("f32", 1024)])
+def test_batch_edge_shapes(H, dtname, d):
+    """Width extremes (one 16-byte vector per row; 256 per row), a graph that
+    is not coarsened at all next to deeper ones, a node in 9,000 hyperedges
+    (split rows with many chunks), zero sweeps and omega = 0 (identity)."""
+    import torch
+    dt = torch.float32 if dtname == "f32" else torch.bfloat16
+    hgs = [_hub_graph(3000, 9000, 1),
+           hypergen.generate(hypergen.CONFIGS["small_2k"]),
+           hypergen.random_small_hypergraph(np.random.default_rng(2), 30, 20, 5)]
+    Gs = []
+    for i, hg in enumerate(hgs):
+        G = H.Graph.from_hypergraph(hg)
+        G.coarsen(min_nodes=10 ** 9 if i == 2 else 100, seed=i)   # graph 2: one level
+        Gs.append(G)
+    assert Gs[2].num_levels == 1 and Gs[0].num_levels > 1
+    with H.Batch(Gs) as B:
+        co, vo, eo = B.offsets()
+        zc = torch.randn((int(co[-1]), d), device="cuda").to(dt)
+        zv = torch.empty((int(vo[-1]), d), dtype=dt, device="cuda")
+        ze = torch.empty((int(eo[-1]), d), dtype=dt, device="cuda")
+        for omega, sweeps in ((0.5, 3), (0.5, 0), (0.0, 2)):
+            B.vcycle(zc, zv, ze, omega, sweeps)
+            torch.cuda.synchronize()
+            for i, G in enumerate(Gs):
+                G.sync_status()
+                n0, m0, _ = G.level_info(0)
+                sv = torch.empty((n0, d), dtype=dt, device="cuda")
+                se = torch.empty((m0, d), dtype=dt, device="cuda")
+                G.vcycle(zc[co[i]:co[i + 1]].contiguous(), sv, se, omega, sweeps)
+                assert torch.equal(sv, zv[vo[i]:vo[i + 1]]) and torch.equal(se, ze[eo[i]:eo[i + 1]])
+    for G in Gs:
+        G.close()
