@@ -344,7 +344,8 @@ typedef struct {
 
 /* A batch over `count` graphs (built and coarsened; all on one device). The
  * batch references the graphs (they must outlive it) and owns its own work
- * lists, buffers, stream and captured graph. */
+ * lists, buffers, stream and captured graph. Coarsening a graph again makes
+ * the batch stale: its later calls return HNV_ERR_STATE. */
 int hnv_batch_create(hnv_graph* const* graphs, int32_t count, hnv_batch** out);
 
 /* Row offsets of the batched buffers (each array count + 1 entries, host):

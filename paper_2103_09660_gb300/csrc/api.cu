@@ -256,6 +256,7 @@ int hnv_coarsen(hnv_graph* g, const hnv_coarsen_params* p, int32_t* n_levels) {
     HNV_FAIL(HNV_ERR_INVALID_ARG, "EXPLICIT policy needs explicit_prio");
   DeviceGuard dg(g->device);
   cudaStream_t s = g->stream;
+  ++g->generation;   // anything built on the old hierarchy (a batch) is stale now
   // drop any previous hierarchy above level 0
   while (g->levels.size() > 1) {
     free_level(&g->levels.back(), s);

@@ -237,6 +237,7 @@ using namespace hnv;
 
 struct hnv_batch {
   std::vector<hnv_graph*> graphs;
+  std::vector<uint64_t> generation;   // each graph's hierarchy generation at creation
   int device = 0;
   cudaStream_t cap_stream = nullptr;
   std::vector<int> top;            // coarsest level of each graph
@@ -711,6 +712,7 @@ int hnv_batch_create(hnv_graph* const* graphs, int32_t count, hnv_batch** out) {
   hnv_batch* b = new (std::nothrow) hnv_batch();
   if (!b) HNV_FAIL(HNV_ERR_OOM, "host allocation failed");
   b->graphs.assign(graphs, graphs + count);
+  for (int32_t i = 0; i < count; ++i) b->generation.push_back(graphs[i]->generation);
   b->device = dev0;
   b->coarse_off.assign(count + 1, 0);
   b->v_off.assign(count + 1, 0);
@@ -752,6 +754,9 @@ int hnv_batch_autotune(hnv_batch* b, hnv_dtype dt, int d, float omega, hnv_batch
   if (!b) HNV_FAIL(HNV_ERR_INVALID_ARG, "batch is NULL");
   if (dt != HNV_F32 && dt != HNV_BF16) HNV_FAIL(HNV_ERR_INVALID_ARG, "unknown dtype");
   if (d < 8 || d > 1024 || d % 8) HNV_FAIL(HNV_ERR_UNSUPPORTED_D, "d must be a multiple of 8 in [8, 1024]");
+  for (size_t i = 0; i < b->graphs.size(); ++i)
+    if (b->graphs[i]->generation != b->generation[i])
+      HNV_FAIL(HNV_ERR_STATE, "graph %zu was coarsened again after the batch was created", i);
   int prev = -1;
   cudaGetDevice(&prev);
   cudaSetDevice(b->device);
@@ -846,6 +851,9 @@ int hnv_batch_vcycle(hnv_batch* b, const void* z_coarsest, void* z_v_out, void* 
   if ((reinterpret_cast<uintptr_t>(z_coarsest) | reinterpret_cast<uintptr_t>(z_v_out) |
        reinterpret_cast<uintptr_t>(z_e_out)) & 15u)
     HNV_FAIL(HNV_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
+  for (size_t i = 0; i < b->graphs.size(); ++i)
+    if (b->graphs[i]->generation != b->generation[i])
+      HNV_FAIL(HNV_ERR_STATE, "graph %zu was coarsened again after the batch was created", i);
   int prev = -1;
   cudaGetDevice(&prev);
   cudaSetDevice(b->device);

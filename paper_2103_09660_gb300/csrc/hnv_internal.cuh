@@ -247,6 +247,7 @@ struct hnv_graph {
   size_t partials_bytes = 0;
   float* jacobi_tmp = nullptr;   // Jacobi: next hyperedge rows
   size_t jacobi_bytes = 0;
+  uint64_t generation = 0;       // bumped whenever the hierarchy is rebuilt
 };
 
 namespace hnv {

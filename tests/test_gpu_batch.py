@@ -163,3 +163,20 @@ def test_batch_edge_shapes(H, dtname, d):
                 assert torch.equal(sv, zv[vo[i]:vo[i + 1]]) and torch.equal(se, ze[eo[i]:eo[i + 1]])
     for G in Gs:
         G.close()
+
+
+def test_batch_goes_stale_when_a_graph_is_coarsened_again(H):
+    import torch
+    hgs, Gs = _graphs(H, 3, seed=9)
+    with H.Batch(Gs) as B:
+        co, vo, eo = B.offsets()
+        zc = torch.zeros((int(co[-1]), 16), device="cuda")
+        zv = torch.zeros((int(vo[-1]), 16), device="cuda")
+        ze = torch.zeros((int(eo[-1]), 16), device="cuda")
+        B.vcycle(zc, zv, ze)
+        Gs[1].coarsen(min_nodes=5, seed=1)
+        with pytest.raises(H.HNVError) as ei:
+            B.vcycle(zc, zv, ze)
+        assert ei.value.code == -8
+    for G in Gs:
+        G.close()

@@ -76,3 +76,24 @@ def test_negative_eps_is_a_fixed_count_and_constants_stop_at_once(H):
         assert 1 <= done <= 50 and (delta <= 1e-2 or done == 50)
         with pytest.raises(H.HNVError):
             G.refine_until(0, a_v, a_e, 0.5, -1, 1e-3)
+
+
+def test_jacobi_mode_stops_where_the_oracle_stops(H):
+    hg = hypergen.generate(hypergen.CONFIGS["small_2k"])
+    lv = oracle_level0(hg)
+    z = np.random.default_rng(3).standard_normal((lv.n + lv.m, 16)).astype(np.float32)
+    z64 = z.astype(np.float64)
+    _, _, _, deltas = O.refine_until(lv, z64[:lv.n], z64[lv.n:], 0.5, 30, -1.0, O.SWEEP_JACOBI)
+    for j in range(5, 29):
+        if min(deltas[:j]) > deltas[j] * 1.05:
+            eps = deltas[j] * 1.02
+            break
+    else:
+        pytest.skip("no clear crossing")
+    rv, re, done, _ = O.refine_until(lv, z64[:lv.n], z64[lv.n:], 0.5, 30, eps, O.SWEEP_JACOBI)
+    with H.Graph.from_hypergraph(hg) as G:
+        zv, ze = _rows(z[:lv.n]), _rows(z[lv.n:])
+        got, _ = G.refine_until(0, zv, ze, 0.5, 30, eps, H.SWEEP_JACOBI)
+        assert got == done
+        assert rel_err(zv.double().cpu().numpy(), rv) < FP32_TOL
+        assert rel_err(ze.double().cpu().numpy(), re) < FP32_TOL
