@@ -197,6 +197,9 @@ struct SplitPlan {
   int4* items = nullptr;              // [n_a + n_b + n_c + n_d + n_chunks]
   int4* long_desc = nullptr;          // [n_mid + n_huge]
   int32_t* zero_rows = nullptr;       // [n_zero]
+  // the neighbours of the class-A rows (at most 4; unused slots 0), one
+  // int4 per class-A item in item order, or null (see build_split_plan)
+  int4* a_members = nullptr;          // [n_a]
 };
 
 struct Level {
@@ -260,8 +263,12 @@ int finish_level(hnv_graph* g, Level* lv);   // derived arrays + plans
 int level_weight_arrays(Level* lv, cudaStream_t s);
 // Split-row work plan of a CSR with `rows` rows; its device allocations are
 // appended to `owned` (freed by whoever owns that list).
+// With idx (the CSR's neighbour lists) and a_max <= 4 the plan also packs
+// the class-A rows' neighbours next to their items (a_members), so that a
+// gather reads a short row's descriptor and neighbours in one step.
 int build_split_plan(hnv_graph* g, std::vector<void*>* owned, const int32_t* ptr, int32_t rows,
-                     SplitPlan* plan, cudaStream_t s, const PlanShape& shape = PlanShape());
+                     SplitPlan* plan, cudaStream_t s, const PlanShape& shape = PlanShape(),
+                     const int32_t* idx = nullptr);
 // Panel plan: the rows of `base` no longer than its class C bound keep their
 // classes and items; the longer rows (listed ascending neighbour IDs in
 // [0, cols)) are cut where their neighbours cross a panel boundary (P equal

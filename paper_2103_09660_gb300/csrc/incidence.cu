@@ -213,6 +213,18 @@ __global__ void fill_row_items(const uint64_t* __restrict__ keys, int32_t begin,
   }
 }
 
+// a_members[i] = the (at most 4) neighbours of class-A item i, 0-padded.
+__global__ void pack_a_members(const int4* __restrict__ items, int32_t n_a,
+                               const int32_t* __restrict__ idx, int4* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_a;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int4 it = items[i];
+    const int32_t b = it.y, len = it.z;
+    out[i] = make_int4(len > 0 ? idx[b] : 0, len > 1 ? idx[b + 1] : 0, len > 2 ? idx[b + 2] : 0,
+                       len > 3 ? idx[b + 3] : 0);
+  }
+}
+
 __global__ void long_chunk_counts(const uint64_t* __restrict__ keys, int32_t begin, int32_t count,
                                   const int32_t* __restrict__ ptr, int32_t T,
                                   int32_t* __restrict__ nch) {
@@ -285,7 +297,8 @@ static int owned_alloc(std::vector<void*>* owned, void** p, size_t bytes, cudaSt
 }
 
 int build_split_plan(hnv_graph* g, std::vector<void*>* owned, const int32_t* ptr, int32_t rows,
-                     SplitPlan* plan, cudaStream_t s, const PlanShape& shape) {
+                     SplitPlan* plan, cudaStream_t s, const PlanShape& shape,
+                     const int32_t* idx) {
   *plan = SplitPlan();
   const int32_t T = plan->T;
   if (rows == 0) return HNV_OK;
@@ -331,6 +344,11 @@ int build_split_plan(hnv_graph* g, std::vector<void*>* owned, const int32_t* ptr
     HNV_CHECK(launch("fill_long", fill_long, grid_for(n_long, 256), 256, 0, s,
                      (const uint64_t*)sorted, off[5], n_long, ptr, T, (const int32_t*)chunk_off,
                      plan->long_desc, plan->items + n_rows_items));
+  }
+  if (idx && shape.a_max <= 4 && plan->n_a > 0) {
+    HNV_CHECK(owned_alloc(owned, (void**)&plan->a_members, sizeof(int4) * (size_t)plan->n_a, s));
+    HNV_CHECK(launch("pack_a_members", pack_a_members, grid_for(plan->n_a, 256), 256, 0, s,
+                     (const int4*)plan->items, plan->n_a, idx, plan->a_members));
   }
   if (plan->n_zero > 0) {
     HNV_CHECK(owned_alloc(owned, (void**)&plan->zero_rows, sizeof(int32_t) * (size_t)plan->n_zero, s));
@@ -535,6 +553,7 @@ int build_panel_plan(hnv_graph* g, std::vector<void*>* owned, const SplitPlan& b
   plan->n_huge = n_split - n_mid;
   plan->n_zero = base.n_zero;
   plan->zero_rows = base.zero_rows;       // shared with `base`, which outlives this plan
+  plan->a_members = base.a_members;       // the class-A items are the base's, in order
   HNV_CHECK(owned_alloc(owned, (void**)&plan->items,
                         sizeof(int4) * ((size_t)n_short + n_panel_items), s));
   if (n_short > 0)
@@ -602,7 +621,8 @@ int finish_level(hnv_graph* g, Level* lv) {
   HNV_CHECK(launch("inv_size", inv_size_kernel, grid_for(m, 256), 256, 0, s, m,
                    (const int32_t*)lv->e_ptr, lv->inv_size_e));
   HNV_CHECK(level_weight_arrays(lv, s));
-  HNV_CHECK(build_split_plan(g, &lv->owned, lv->e_ptr, m, &lv->planE, s));
+  HNV_CHECK(build_split_plan(g, &lv->owned, lv->e_ptr, m, &lv->planE, s, PlanShape(),
+                             lv->e_nodes));
   HNV_CHECK(build_split_plan(g, &lv->owned, lv->v_ptr, n, &lv->planV, s));
   return HNV_OK;
 }

@@ -53,6 +53,37 @@ gather_kernel(const int4* __restrict__ items, int32_t n_items, const int32_t* __
   }
 }
 
+// gather_kernel for the class-A rows of an unweighted side whose plan packs
+// their neighbours (SplitPlan::a_members): a group reads its row's
+// descriptor and neighbour indices side by side instead of one after the
+// other, which takes a dependent load off the chain of these short rows.
+template <typename T, int G, int VPL>
+__global__ void __launch_bounds__(256)
+gather_packed_kernel(const int4* __restrict__ items, const int4* __restrict__ members,
+                     int32_t n_items, const int32_t* __restrict__ idx,
+                     const float* __restrict__ inv_norm, const uint4* __restrict__ src,
+                     const uint4* self_in, uint4* out, int32_t dv, float keep, float scale,
+                     float* __restrict__ partials) {
+  constexpr int R = 32 / G;
+  const int lane = threadIdx.x & 31;
+  const int grp = lane / G;
+  const int lg = lane & (G - 1);
+  const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t wbase = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * R;
+       wbase < n_items; wbase += warps_total * R) {
+    const int64_t item = wbase + grp;
+    int4 it = make_int4(-1, 0, 0, -1);
+    int4 mem = make_int4(0, 0, 0, 0);
+    if (item < n_items) {
+      it = __ldg(items + item);
+      mem = __ldg(members + item);
+    }
+    const int32_t idx0 = lg == 0 ? mem.x : lg == 1 ? mem.y : lg == 2 ? mem.z : mem.w;
+    dev::gather_item<T, G, VPL, false, true>(it, lg, idx, nullptr, inv_norm, src, self_in, out,
+                                             dv, keep, scale, partials, idx0);
+  }
+}
+
 // Reduces the chunk partials of split rows. Blocks [0, mid_blocks) give one
 // warp to each of the first n_mid rows (at most kMidChunks chunks); each
 // later block takes one of the n_huge rows (slices of the block sum
@@ -162,6 +193,37 @@ int launch_items(const HalfSweep& h, const int4* items, int32_t n_items, const v
                 dv, keep, scale, partials);
 }
 
+template <typename T, int G, int VPL>
+int launch_packed(const HalfSweep& h, const int4* items, const int4* members, int32_t n_items,
+                  const void* src, const void* self_in, void* out, int dv, float keep,
+                  float scale, float* partials, cudaStream_t s) {
+  if (n_items <= 0) return HNV_OK;
+  constexpr int R = 32 / G;
+  const int64_t warps = ((int64_t)n_items + R - 1) / R;
+  const int64_t blocks64 = (warps + 7) / 8;
+  const unsigned blocks = (unsigned)(blocks64 > 0x7fffffff ? 0x7fffffff : blocks64);
+  return launch("gather_packed", gather_packed_kernel<T, G, VPL>, blocks, 256, 0, s, items,
+                members, n_items, h.idx, h.inv_norm, (const uint4*)src, (const uint4*)self_in,
+                (uint4*)out, dv, keep, scale, partials);
+}
+
+// 1: no packed variant for (G, VPL) (not an error code); the caller takes
+// the regular kernel. The packed rows have at most 4 members, so G >= 4.
+template <typename T>
+int launch_packed_dispatch(int G, int VPL, const HalfSweep& h, const int4* items,
+                           const int4* members, int32_t n_items, const void* src,
+                           const void* self_in, void* out, int dv, float keep, float scale,
+                           float* partials, cudaStream_t s) {
+#define HNV_PCASE(g, v)                                                                      \
+  if (G == g && VPL == v)                                                                    \
+    return launch_packed<T, g, v>(h, items, members, n_items, src, self_in, out, dv, keep,  \
+                                  scale, partials, s);
+  HNV_PCASE(4, 1) HNV_PCASE(8, 1) HNV_PCASE(8, 2) HNV_PCASE(8, 4)
+  HNV_PCASE(16, 1) HNV_PCASE(16, 2) HNV_PCASE(16, 4) HNV_PCASE(32, 1) HNV_PCASE(32, 2)
+#undef HNV_PCASE
+  return 1;
+}
+
 template <typename T>
 int launch_items_dispatch(int G, int VPL, const HalfSweep& h, const int4* items, int32_t n_items,
                           const void* src, const void* self_in, void* out, int dv, float keep,
@@ -217,8 +279,14 @@ int run_half(const HalfSweep& h, const void* src, const void* self_in, void* out
     for (int c = 0; c < 3; ++c) {
       const int G = group_lanes(cls_lanes[c], dv);
       const int VPL = next_pow2((dv + G - 1) / G);
-      HNV_CHECK(launch_items_dispatch<T>(G, VPL, h, items + off, counts[c], src, self_in, out, dv,
-                                         keep, scale, partials, s));
+      int rc = 1;
+      if (c == 0 && p.a_members && !h.inc_w)
+        rc = launch_packed_dispatch<T>(G, VPL, h, items, p.a_members, counts[0], src, self_in, out,
+                                       dv, keep, scale, partials, s);
+      if (rc == 1)
+        rc = launch_items_dispatch<T>(G, VPL, h, items + off, counts[c], src, self_in, out, dv,
+                                      keep, scale, partials, s);
+      HNV_CHECK(rc);
       off += counts[c];
     }
   }

@@ -61,13 +61,15 @@ struct VecT<__nv_bfloat16> {
 //   row item:  out[row] = keep * self[row] + scale * norm[row] * sum_k wgt_k src[idx_k]
 //   chunk:     partials[slot] = sum_k wgt_k src[idx_k]   (float32)
 // norm (inv_norm) may be null (1); with keep == 0 the own row is not read.
-template <typename T, int G, int VPL, bool WEIGHTED>
+// PRE: the caller supplies this lane's first neighbour index (incidence
+// beg + lg, any value where lg >= len) in idx0 instead of it being loaded.
+template <typename T, int G, int VPL, bool WEIGHTED, bool PRE = false>
 __device__ __forceinline__ void gather_item(int4 it, int lg, const int32_t* __restrict__ idx,
                                             const float* __restrict__ inc_w,
                                             const float* __restrict__ inv_norm,
                                             const uint4* __restrict__ src, const uint4* self_in,
                                             uint4* out, int32_t dv, float keep, float scale,
-                                            float* __restrict__ partials) {
+                                            float* __restrict__ partials, int32_t idx0 = 0) {
   using V = VecT<T>;
   constexpr int N = V::N;
   // row loads in flight per lane (the weighted variant also holds a weight
@@ -100,7 +102,8 @@ __device__ __forceinline__ void gather_item(int4 it, int lg, const int32_t* __re
     for (int32_t off = 0; off < maxlen; off += G) {
       const int32_t mine = len - off;
       const bool have = lg < mine;
-      const int32_t my_idx = have ? __ldg(idx + beg + off + lg) : 0;
+      const int32_t my_idx =
+          have ? ((PRE && off == 0) ? idx0 : __ldg(idx + beg + off + lg)) : 0;
       float my_w = 0.f;
       if (WEIGHTED) my_w = have ? __ldg(inc_w + beg + off + lg) : 0.f;
       const int32_t cnt = min(G, maxlen - off);
