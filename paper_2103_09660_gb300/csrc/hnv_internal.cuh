@@ -200,6 +200,8 @@ struct SplitPlan {
   // the neighbours of the class-A rows (at most 4; unused slots 0), one
   // int4 per class-A item in item order, or null (see build_split_plan)
   int4* a_members = nullptr;          // [n_a]
+  // the same for the class-B rows (at most 16 neighbours, 16 slots each)
+  int32_t* b_members = nullptr;       // [n_b * 16]
 };
 
 struct Level {
@@ -263,9 +265,10 @@ int finish_level(hnv_graph* g, Level* lv);   // derived arrays + plans
 int level_weight_arrays(Level* lv, cudaStream_t s);
 // Split-row work plan of a CSR with `rows` rows; its device allocations are
 // appended to `owned` (freed by whoever owns that list).
-// With idx (the CSR's neighbour lists) and a_max <= 4 the plan also packs
-// the class-A rows' neighbours next to their items (a_members), so that a
-// gather reads a short row's descriptor and neighbours in one step.
+// With idx (the CSR's neighbour lists) and a_max <= 4 (b_max <= 16) the
+// plan also packs the class-A (class-B) rows' neighbours next to their items
+// (a_members, b_members), so that a gather reads a short row's descriptor
+// and neighbours in one step.
 int build_split_plan(hnv_graph* g, std::vector<void*>* owned, const int32_t* ptr, int32_t rows,
                      SplitPlan* plan, cudaStream_t s, const PlanShape& shape = PlanShape(),
                      const int32_t* idx = nullptr);

@@ -225,6 +225,18 @@ __global__ void pack_a_members(const int4* __restrict__ items, int32_t n_a,
   }
 }
 
+// out[16 i + j] = neighbour j of class-B item i (j < its length), else 0.
+__global__ void pack_b_members(const int4* __restrict__ items, int32_t n_b,
+                               const int32_t* __restrict__ idx, int32_t* __restrict__ out) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)n_b * 16;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t >> 4;
+    const int32_t j = (int32_t)(t & 15);
+    const int4 it = items[i];
+    out[t] = j < it.z ? idx[it.y + j] : 0;
+  }
+}
+
 __global__ void long_chunk_counts(const uint64_t* __restrict__ keys, int32_t begin, int32_t count,
                                   const int32_t* __restrict__ ptr, int32_t T,
                                   int32_t* __restrict__ nch) {
@@ -349,6 +361,13 @@ int build_split_plan(hnv_graph* g, std::vector<void*>* owned, const int32_t* ptr
     HNV_CHECK(owned_alloc(owned, (void**)&plan->a_members, sizeof(int4) * (size_t)plan->n_a, s));
     HNV_CHECK(launch("pack_a_members", pack_a_members, grid_for(plan->n_a, 256), 256, 0, s,
                      (const int4*)plan->items, plan->n_a, idx, plan->a_members));
+  }
+  if (idx && shape.b_max <= 16 && plan->n_b > 0) {
+    HNV_CHECK(owned_alloc(owned, (void**)&plan->b_members,
+                          sizeof(int32_t) * 16 * (size_t)plan->n_b, s));
+    HNV_CHECK(launch("pack_b_members", pack_b_members, grid_for((int64_t)plan->n_b * 16, 256), 256,
+                     0, s, (const int4*)(plan->items + plan->n_a), plan->n_b, idx,
+                     plan->b_members));
   }
   if (plan->n_zero > 0) {
     HNV_CHECK(owned_alloc(owned, (void**)&plan->zero_rows, sizeof(int32_t) * (size_t)plan->n_zero, s));
@@ -553,7 +572,8 @@ int build_panel_plan(hnv_graph* g, std::vector<void*>* owned, const SplitPlan& b
   plan->n_huge = n_split - n_mid;
   plan->n_zero = base.n_zero;
   plan->zero_rows = base.zero_rows;       // shared with `base`, which outlives this plan
-  plan->a_members = base.a_members;       // the class-A items are the base's, in order
+  plan->a_members = base.a_members;       // the class-A and B items are the base's, in order
+  plan->b_members = base.b_members;
   HNV_CHECK(owned_alloc(owned, (void**)&plan->items,
                         sizeof(int4) * ((size_t)n_short + n_panel_items), s));
   if (n_short > 0)

@@ -59,6 +59,33 @@ gather_kernel(const int4* __restrict__ items, int32_t n_items, const int32_t* __
 // other, which takes a dependent load off the chain of these short rows.
 template <typename T, int G, int VPL>
 __global__ void __launch_bounds__(256)
+gather_packed16_kernel(const int4* __restrict__ items, const int32_t* __restrict__ members,
+                       int32_t n_items, const int32_t* __restrict__ idx,
+                       const float* __restrict__ inv_norm, const uint4* __restrict__ src,
+                       const uint4* self_in, uint4* out, int32_t dv, float keep, float scale,
+                       float* __restrict__ partials) {
+  static_assert(G >= 16, "a group holds the 16 packed neighbours one per lane");
+  constexpr int R = 32 / G;
+  const int lane = threadIdx.x & 31;
+  const int grp = lane / G;
+  const int lg = lane & (G - 1);
+  const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t wbase = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * R;
+       wbase < n_items; wbase += warps_total * R) {
+    const int64_t item = wbase + grp;
+    int4 it = make_int4(-1, 0, 0, -1);
+    int32_t idx0 = 0;
+    if (item < n_items) {
+      it = __ldg(items + item);
+      if (lg < 16) idx0 = __ldg(members + item * 16 + lg);
+    }
+    dev::gather_item<T, G, VPL, false, true>(it, lg, idx, nullptr, inv_norm, src, self_in, out,
+                                             dv, keep, scale, partials, idx0);
+  }
+}
+
+template <typename T, int G, int VPL>
+__global__ void __launch_bounds__(256)
 gather_packed_kernel(const int4* __restrict__ items, const int4* __restrict__ members,
                      int32_t n_items, const int32_t* __restrict__ idx,
                      const float* __restrict__ inv_norm, const uint4* __restrict__ src,
@@ -194,6 +221,20 @@ int launch_items(const HalfSweep& h, const int4* items, int32_t n_items, const v
 }
 
 template <typename T, int G, int VPL>
+int launch_packed16(const HalfSweep& h, const int4* items, const int32_t* members,
+                    int32_t n_items, const void* src, const void* self_in, void* out, int dv,
+                    float keep, float scale, float* partials, cudaStream_t s) {
+  if (n_items <= 0) return HNV_OK;
+  constexpr int R = 32 / G;
+  const int64_t warps = ((int64_t)n_items + R - 1) / R;
+  const int64_t blocks64 = (warps + 7) / 8;
+  const unsigned blocks = (unsigned)(blocks64 > 0x7fffffff ? 0x7fffffff : blocks64);
+  return launch("gather_packed16", gather_packed16_kernel<T, G, VPL>, blocks, 256, 0, s, items,
+                members, n_items, h.idx, h.inv_norm, (const uint4*)src, (const uint4*)self_in,
+                (uint4*)out, dv, keep, scale, partials);
+}
+
+template <typename T, int G, int VPL>
 int launch_packed(const HalfSweep& h, const int4* items, const int4* members, int32_t n_items,
                   const void* src, const void* self_in, void* out, int dv, float keep,
                   float scale, float* partials, cudaStream_t s) {
@@ -219,6 +260,21 @@ int launch_packed_dispatch(int G, int VPL, const HalfSweep& h, const int4* items
     return launch_packed<T, g, v>(h, items, members, n_items, src, self_in, out, dv, keep,  \
                                   scale, partials, s);
   HNV_PCASE(4, 1) HNV_PCASE(8, 1) HNV_PCASE(8, 2) HNV_PCASE(8, 4)
+  HNV_PCASE(16, 1) HNV_PCASE(16, 2) HNV_PCASE(16, 4) HNV_PCASE(32, 1) HNV_PCASE(32, 2)
+#undef HNV_PCASE
+  return 1;
+}
+
+// As launch_packed_dispatch for the class-B rows (16 packed slots, G >= 16).
+template <typename T>
+int launch_packed16_dispatch(int G, int VPL, const HalfSweep& h, const int4* items,
+                             const int32_t* members, int32_t n_items, const void* src,
+                             const void* self_in, void* out, int dv, float keep, float scale,
+                             float* partials, cudaStream_t s) {
+#define HNV_PCASE(g, v)                                                                      \
+  if (G == g && VPL == v)                                                                    \
+    return launch_packed16<T, g, v>(h, items, members, n_items, src, self_in, out, dv, keep,\
+                                    scale, partials, s);
   HNV_PCASE(16, 1) HNV_PCASE(16, 2) HNV_PCASE(16, 4) HNV_PCASE(32, 1) HNV_PCASE(32, 2)
 #undef HNV_PCASE
   return 1;
@@ -283,6 +339,9 @@ int run_half(const HalfSweep& h, const void* src, const void* self_in, void* out
       if (c == 0 && p.a_members && !h.inc_w)
         rc = launch_packed_dispatch<T>(G, VPL, h, items, p.a_members, counts[0], src, self_in, out,
                                        dv, keep, scale, partials, s);
+      if (c == 1 && p.b_members && !h.inc_w)
+        rc = launch_packed16_dispatch<T>(G, VPL, h, items + off, p.b_members, counts[1], src,
+                                         self_in, out, dv, keep, scale, partials, s);
       if (rc == 1)
         rc = launch_items_dispatch<T>(G, VPL, h, items + off, counts[c], src, self_in, out, dv,
                                       keep, scale, partials, s);
