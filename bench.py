@@ -262,7 +262,12 @@ def traffic_summary(csv_path):
     for lid in sorted(launches):
         rec = launches[lid]
         name = rec["name"]
-        if "gather_kernel<" in name and "batched" not in name:
+        if "gather_packed" in name:             # the packed short rows: hyperedge side
+            side = "E"
+            if side != phase:
+                acc[side][2] += 1
+            phase = side
+        elif "gather_kernel<" in name and "batched" not in name:
             side = "V" if name.split("<", 1)[1].split(">", 1)[0].rstrip().endswith("1") else "E"
             if side != phase:
                 acc[side][2] += 1
