@@ -37,6 +37,14 @@ void destroy_graph(hnv_graph* g) {
   dev_free(g->d_err, s);
   dev_free(g->d_buf, s);
   cudaStreamSynchronize(s);
+  for (int i = 0; i < 2; ++i) {
+    if (g->aux[i]) {
+      cudaStreamSynchronize(g->aux[i]);
+      cudaStreamDestroy(g->aux[i]);
+    }
+    if (g->join_ev[i]) cudaEventDestroy(g->join_ev[i]);
+  }
+  if (g->fork_ev) cudaEventDestroy(g->fork_ev);
   if (g->h_buf) cudaFreeHost(g->h_buf);
   delete g;
 }
@@ -193,6 +201,17 @@ int hnv_build_incidence(int32_t n_nodes, int32_t n_edges, const int64_t* edge_pt
     }
     if ((rc = dev_alloc((void**)&g->d_err, sizeof(int32_t), s)) != HNV_OK) break;
     if ((rc = dev_alloc((void**)&g->d_buf, 64 * sizeof(int32_t), s)) != HNV_OK) break;
+    {
+      cudaError_t e = cudaEventCreateWithFlags(&g->fork_ev, cudaEventDisableTiming);
+      for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&g->aux[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->join_ev[i], cudaEventDisableTiming);
+      }
+      if (e != cudaSuccess) {
+        rc = cuda_status(e, "side streams");
+        break;
+      }
+    }
     if (cudaMemsetAsync(g->d_err, 0, sizeof(int32_t), s) != cudaSuccess) {
       rc = cuda_status(cudaGetLastError(), "cudaMemsetAsync");
       break;

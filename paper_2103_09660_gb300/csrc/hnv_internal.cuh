@@ -253,6 +253,11 @@ struct hnv_graph {
   float* jacobi_tmp = nullptr;   // Jacobi: next hyperedge rows
   size_t jacobi_bytes = 0;
   uint64_t generation = 0;       // bumped whenever the hierarchy is rebuilt
+  // side streams on which a half-sweep's row classes run concurrently
+  // (forked from and joined back into the caller's stream)
+  cudaStream_t aux[2] = {nullptr, nullptr};
+  cudaEvent_t fork_ev = nullptr;
+  cudaEvent_t join_ev[2] = {nullptr, nullptr};
 };
 
 namespace hnv {

@@ -185,6 +185,8 @@ struct HalfSweep {
   int64_t self_rows;       // rows of this side's table
   int32_t* err;            // device error word (bounded waits)
   bool allow_tma = true;   // forward relaxations only
+  // optional: run the row classes concurrently on these side streams
+  const hnv_graph* conc = nullptr;
 };
 
 // Which gather path the half-sweeps use. The default is the per-lane load
@@ -331,6 +333,18 @@ int run_half(const HalfSweep& h, const void* src, const void* self_in, void* out
     // d = 128: hyperedge half-sweeps 4-7% faster than with 8 lanes).
     const int cls_lanes[3] = {16, 16, 32};
     const int32_t counts[3] = {p.n_a, p.n_b, p.n_c + p.n_d + p.n_chunks};
+    // The classes touch disjoint rows of `out` (chunks only write partials),
+    // so they may run at once: classes B and the rest go to side streams
+    // forked from s and joined back before the split-row reduction.
+    const bool conc = h.conc && counts[1] > 0 && counts[2] > 0;
+    cudaStream_t cs[3] = {s, s, s};
+    if (conc) {
+      HNV_CUDA(cudaEventRecord(h.conc->fork_ev, s));
+      for (int i = 0; i < 2; ++i) {
+        HNV_CUDA(cudaStreamWaitEvent(h.conc->aux[i], h.conc->fork_ev, 0));
+        cs[i + 1] = h.conc->aux[i];
+      }
+    }
     int32_t off = 0;
     for (int c = 0; c < 3; ++c) {
       const int G = group_lanes(cls_lanes[c], dv);
@@ -338,15 +352,21 @@ int run_half(const HalfSweep& h, const void* src, const void* self_in, void* out
       int rc = 1;
       if (c == 0 && p.a_members && !h.inc_w)
         rc = launch_packed_dispatch<T>(G, VPL, h, items, p.a_members, counts[0], src, self_in, out,
-                                       dv, keep, scale, partials, s);
+                                       dv, keep, scale, partials, cs[c]);
       if (c == 1 && p.b_members && !h.inc_w)
         rc = launch_packed16_dispatch<T>(G, VPL, h, items + off, p.b_members, counts[1], src,
-                                         self_in, out, dv, keep, scale, partials, s);
+                                         self_in, out, dv, keep, scale, partials, cs[c]);
       if (rc == 1)
         rc = launch_items_dispatch<T>(G, VPL, h, items + off, counts[c], src, self_in, out, dv,
-                                      keep, scale, partials, s);
+                                      keep, scale, partials, cs[c]);
       HNV_CHECK(rc);
       off += counts[c];
+    }
+    if (conc) {
+      for (int i = 0; i < 2; ++i) {
+        HNV_CUDA(cudaEventRecord(h.conc->join_ev[i], h.conc->aux[i]));
+        HNV_CUDA(cudaStreamWaitEvent(s, h.conc->join_ev[i], 0));
+      }
     }
   }
   if (p.n_mid + p.n_huge > 0) {
@@ -419,8 +439,9 @@ int refine_level(hnv_graph* g, int level, void* z_v, void* z_e, int dtype, int d
   if (mode == HNV_SWEEP_JACOBI)
     HNV_CHECK(ensure_scratch(&g->jacobi_tmp, &g->jacobi_bytes,
                              es * ((size_t)lv.m > 0 ? lv.m : 1) * d, s));
-  const HalfSweep E{lv.e_nodes, nullptr, lv.inv_size_e, planE, lv.n, lv.m, g->d_err};
-  const HalfSweep V{lv.v_edges, lv.v_w, lv.inv_deg_v, planV, lv.m, lv.n, g->d_err};
+  HalfSweep E{lv.e_nodes, nullptr, lv.inv_size_e, planE, lv.n, lv.m, g->d_err};
+  HalfSweep V{lv.v_edges, lv.v_w, lv.inv_deg_v, planV, lv.m, lv.n, g->d_err};
+  if (g->aux[0] && g->aux[1]) E.conc = V.conc = g;
   const double n = lv.n, m = lv.m, nnz = (double)lv.nnz;
   const double bytesE = (double)es * (n * d + 2.0 * m * d) + 4.0 * (nnz + 2.0 * m + 1.0);
   const double bytesV = (double)es * (m * d + 2.0 * n * d) + 4.0 * (2.0 * nnz + 2.0 * n + 1.0);
