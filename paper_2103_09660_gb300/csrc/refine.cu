@@ -314,6 +314,21 @@ int group_lanes(int cls, int dv) {
   return g > 32 ? 32 : g;
 }
 
+// The split-row reduction of a plan (nothing if it has no split rows).
+template <typename T>
+int launch_finalize(const HalfSweep& h, const SplitPlan& p, float* partials, const void* self_in,
+                    void* out, int dv, float keep, float scale, cudaStream_t s) {
+  if (p.n_mid + p.n_huge == 0) return HNV_OK;
+  constexpr int N = VecT<T>::N;
+  const int32_t mid_blocks = (p.n_mid + kFinThreads / 32 - 1) / (kFinThreads / 32);
+  const int S = kFinThreads / dv;
+  const size_t smem = sizeof(float) * (size_t)S * dv * N;
+  return launch("finalize", finalize_kernel<T>, (unsigned)(mid_blocks + p.n_huge), kFinThreads,
+                smem, s, (const int4*)p.long_desc, p.n_mid, p.n_huge, mid_blocks,
+                (const float*)partials, h.inv_norm, (const uint4*)self_in, (uint4*)out, dv, keep,
+                scale);
+}
+
 template <typename T>
 int run_half(const HalfSweep& h, const void* src, const void* self_in, void* out, int d,
              float keep, float scale, float* partials, cudaStream_t s) {
@@ -325,6 +340,7 @@ int run_half(const HalfSweep& h, const void* src, const void* self_in, void* out
     HNV_CHECK(tma_half_sweep(p, h.idx, h.inc_w, h.inv_norm, (const float*)src, h.src_rows,
                              (const float*)self_in, (float*)out, h.self_rows, d, scale, partials,
                              h.err, s));
+    HNV_CHECK(launch_finalize<T>(h, p, partials, self_in, out, dv, keep, scale, s));
   } else {
     const int4* items = p.items;
     // lanes per item of classes A, B and the rest. With 16 lanes on rows of
@@ -362,21 +378,15 @@ int run_half(const HalfSweep& h, const void* src, const void* self_in, void* out
       HNV_CHECK(rc);
       off += counts[c];
     }
+    // the split rows' reduction needs only the chunks (the last class), and
+    // writes only split rows: it follows that class on its stream
+    HNV_CHECK(launch_finalize<T>(h, p, partials, self_in, out, dv, keep, scale, cs[2]));
     if (conc) {
       for (int i = 0; i < 2; ++i) {
         HNV_CUDA(cudaEventRecord(h.conc->join_ev[i], h.conc->aux[i]));
         HNV_CUDA(cudaStreamWaitEvent(s, h.conc->join_ev[i], 0));
       }
     }
-  }
-  if (p.n_mid + p.n_huge > 0) {
-    const int32_t mid_blocks = (p.n_mid + kFinThreads / 32 - 1) / (kFinThreads / 32);
-    const int S = kFinThreads / dv;
-    const size_t smem = sizeof(float) * (size_t)S * dv * N;
-    HNV_CHECK(launch("finalize", finalize_kernel<T>, (unsigned)(mid_blocks + p.n_huge),
-                     kFinThreads, smem, s, (const int4*)p.long_desc, p.n_mid, p.n_huge,
-                     mid_blocks, (const float*)partials, h.inv_norm, (const uint4*)self_in,
-                     (uint4*)out, dv, keep, scale));
   }
   if (self_in != out && p.n_zero > 0)
     HNV_CHECK(launch("copy_rows", copy_rows_kernel, grid_for((int64_t)p.n_zero * dv, 256), 256, 0,
