@@ -26,6 +26,12 @@
  *    installed with hnv_set_allocator().
  *  - IDs are int32: n, m < 2^31 and every level's incidence count
  *    nnz < 2^31 (HNV_ERR_TOO_LARGE otherwise).
+ *  - One graph (or one batch) holds scratch that its calls share (split-row
+ *    partials, a small device word buffer, two side streams on which a
+ *    half-sweep's row classes run, forked from and joined back into the
+ *    caller's stream). Calls on the same graph or batch must therefore not
+ *    run concurrently from several host threads, or on streams whose work
+ *    overlaps; different graphs are independent.
  */
 #ifndef HNV_H_
 #define HNV_H_
