@@ -240,6 +240,10 @@ struct hnv_batch {
   std::vector<uint64_t> generation;   // each graph's hierarchy generation at creation
   int device = 0;
   cudaStream_t cap_stream = nullptr;
+  // side streams: a half-sweep's row classes run concurrently (see enqueue_half)
+  cudaStream_t aux[2] = {nullptr, nullptr};
+  cudaEvent_t fork_ev = nullptr;
+  cudaEvent_t join_ev[2] = {nullptr, nullptr};
   std::vector<int> top;            // coarsest level of each graph
   int Lmax = 0;
   PlanShape shape;
@@ -572,19 +576,33 @@ int launch_batched_dispatch(int G, int VPL, const BSide& B, int64_t first, int32
   HNV_FAIL(HNV_ERR_UNSUPPORTED_D, "no batched gather variant for G=%d VPL=%d", G, VPL);
 }
 
+// The three row classes touch disjoint rows (chunks write only partials):
+// classes B and the rest run on the batch's side streams, forked from s and
+// joined back (inside a capture these become parallel branches of the
+// graph); the split-row reduction follows the last class on its stream.
 template <typename T>
 int enqueue_half(const hnv_batch* b, const BSide& B, int dv, float omega, cudaStream_t s) {
   const float keep = 1.0f - omega;
+  const bool conc = b->aux[0] && b->aux[1] && B.n_cls[1] > 0 && B.n_cls[2] > 0;
+  cudaStream_t cs[3] = {s, s, s};
+  if (conc) {
+    HNV_CUDA(cudaEventRecord(b->fork_ev, s));
+    for (int i = 0; i < 2; ++i) {
+      HNV_CUDA(cudaStreamWaitEvent(b->aux[i], b->fork_ev, 0));
+      cs[i + 1] = b->aux[i];
+    }
+  }
   int64_t first = 0;
   for (int c = 0; c < 3; ++c) {
     const int G = class_lanes(b, c, dv);
     const int VPL = next_pow2((dv + G - 1) / G);
     if (B.weighted)
-      HNV_CHECK((launch_batched_dispatch<T, true>(G, VPL, B, first, B.n_cls[c], dv, keep, omega, s)));
+      HNV_CHECK((launch_batched_dispatch<T, true>(G, VPL, B, first, B.n_cls[c], dv, keep, omega, cs[c])));
     else
-      HNV_CHECK((launch_batched_dispatch<T, false>(G, VPL, B, first, B.n_cls[c], dv, keep, omega, s)));
+      HNV_CHECK((launch_batched_dispatch<T, false>(G, VPL, B, first, B.n_cls[c], dv, keep, omega, cs[c])));
     first += B.n_cls[c];
   }
+  s = cs[2];   // the reduction follows the chunks' class
   if (B.n_mid + B.n_huge > 0) {
     constexpr int N = dev::VecT<T>::N;
     const int32_t mid_blocks = (B.n_mid + kFinThreads / 32 - 1) / (kFinThreads / 32);
@@ -594,6 +612,13 @@ int enqueue_half(const hnv_batch* b, const BSide& B, int dv, float omega, cudaSt
                      (unsigned)(mid_blocks + B.n_huge), kFinThreads, smem, s,
                      (const int4*)B.long_desc, (const int32_t*)B.long_g, B.n_mid, B.n_huge,
                      mid_blocks, (const GraphSide*)B.sides, B.n_graphs, dv, keep, omega));
+  }
+  if (conc) {
+    cudaStream_t origin = cs[0];
+    for (int i = 0; i < 2; ++i) {
+      HNV_CUDA(cudaEventRecord(b->join_ev[i], b->aux[i]));
+      HNV_CUDA(cudaStreamWaitEvent(origin, b->join_ev[i], 0));
+    }
   }
   return HNV_OK;
 }
@@ -730,9 +755,14 @@ int hnv_batch_create(hnv_graph* const* graphs, int32_t count, hnv_batch** out) {
   cudaGetDevice(&prev);
   cudaSetDevice(dev0);
   cudaError_t e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    e = cudaStreamCreateWithFlags(&b->aux[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join_ev[i], cudaEventDisableTiming);
+  }
   if (prev >= 0) cudaSetDevice(prev);
   if (e != cudaSuccess) {
-    delete b;
+    hnv_batch_free(b);
     return cuda_status(e, "cudaStreamCreate");
   }
   *out = b;
@@ -924,10 +954,20 @@ void hnv_batch_free(hnv_batch* b) {
   int prev = -1;
   cudaGetDevice(&prev);
   cudaSetDevice(b->device);
-  free_steps(b, b->cap_stream);
-  free_list(b->plan_owned, b->cap_stream);
-  cudaStreamSynchronize(b->cap_stream);
-  cudaStreamDestroy(b->cap_stream);
+  if (b->cap_stream) {
+    free_steps(b, b->cap_stream);
+    free_list(b->plan_owned, b->cap_stream);
+    cudaStreamSynchronize(b->cap_stream);
+    cudaStreamDestroy(b->cap_stream);
+  }
+  for (int i = 0; i < 2; ++i) {
+    if (b->aux[i]) {
+      cudaStreamSynchronize(b->aux[i]);
+      cudaStreamDestroy(b->aux[i]);
+    }
+    if (b->join_ev[i]) cudaEventDestroy(b->join_ev[i]);
+  }
+  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
   if (prev >= 0) cudaSetDevice(prev);
   delete b;
 }
