@@ -177,7 +177,24 @@ assign_long_kernel(const int32_t* __restrict__ long_rows, const int32_t* __restr
     float bs = -INFINITY;
     uint64_t bp = ~0ull;
     int32_t be = 0x7fffffff;
-    for (int64_t k = b + threadIdx.x; k < end; k += kLongThreads) {
+    // four incidences per step keep four independent load chains in flight
+    // (the minimum of a total order does not depend on the visiting order)
+    int64_t k = b + threadIdx.x;
+    for (; k + 3 * kLongThreads < end; k += 4 * kLongThreads) {
+      int32_t e[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) e[u] = v_edges[k + u * kLongThreads];
+      uint64_t pr[4];
+      float sc[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        pr[u] = prio[e[u]];
+        sc[u] = score ? score[k + u * kLongThreads] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) lex_min(bs, bp, be, sc[u], pr[u], e[u]);
+    }
+    for (; k < end; k += kLongThreads) {
       const int32_t e = v_edges[k];
       lex_min(bs, bp, be, score ? score[k] : 0.f, prio[e], e);
     }
