@@ -350,8 +350,12 @@ typedef struct {
 
 /* A batch over `count` graphs (built and coarsened; all on one device). The
  * batch references the graphs (they must outlive it) and owns its own work
- * lists, buffers, stream and captured graph. Coarsening a graph again makes
- * the batch stale: its later calls return HNV_ERR_STATE. */
+ * lists, buffers, streams and captured graph. Coarsening a graph again makes
+ * the batch stale: its later calls return HNV_ERR_STATE.
+ *   graphs [count] : host array of graph handles; count >= 1
+ *   out            : receives the batch (NULL on failure)
+ * Errors: HNV_ERR_INVALID_ARG (NULL, count < 1, graphs on different
+ * devices), HNV_ERR_OOM, HNV_ERR_CUDA. Synchronises each graph's stream. */
 int hnv_batch_create(hnv_graph* const* graphs, int32_t count, hnv_batch** out);
 
 /* Row offsets of the batched buffers (each array count + 1 entries, host):
@@ -369,11 +373,23 @@ int hnv_batch_autotune(hnv_batch* b, hnv_dtype dt, int d, float omega, hnv_batch
 /* The two-phase V-cycle of every graph of the batch (device buffers laid out
  * as hnv_batch_offsets says; d % 8 == 0). With use_cuda_graph the whole
  * cycle is captured once (per buffers, dtype, d, omega and sweeps) and
- * replayed on `stream`. */
+ * replayed on `stream`.
+ *   z_coarsest [coarsest_rows[count] x d] : read
+ *   z_v_out [node_rows[count] x d], z_e_out [edge_rows[count] x d] : written
+ *   (device, 16-byte aligned, caller-owned; the batch keeps work lists built
+ *   for these pointers until they change)
+ * Errors: HNV_ERR_INVALID_ARG (NULL or misaligned buffer, omega outside
+ * [0, 1], sweeps < 0), HNV_ERR_UNSUPPORTED_D, HNV_ERR_STATE (a graph was
+ * coarsened again), HNV_ERR_OOM, HNV_ERR_CUDA. Device-side checks of the
+ * work items report through hnv_sync_status of the graphs. Asynchronous on
+ * `stream` after the first call for a set of buffers (which builds the work
+ * lists and synchronises its own stream). */
 int hnv_batch_vcycle(hnv_batch* b, const void* z_coarsest, void* z_v_out, void* z_e_out,
                      hnv_dtype dt, int d, float omega, int sweeps_per_level, int use_cuda_graph,
                      hnv_stream_t stream);
 
+/* Releases the batch (its buffers, streams and captured graph; not the
+ * graphs). Synchronises the batch's streams. NULL is a no-op. */
 void hnv_batch_free(hnv_batch* b);
 
 /* Synchronises `stream` and reports device-side failures of the graph's
