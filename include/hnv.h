@@ -278,7 +278,10 @@ int hnv_vcycle(hnv_graph* g, const void* z_coarsest, void* z_v_out, void* z_e_ou
  *   allocate): on a level where hnv_refine cuts rows into panels the two
  *   agree to float32 rounding, elsewhere bit for bit.
  *   The first call on a device looks up the array's device address (once per
- *   device, under a lock). All calls share the one array and it keeps the
+ *   device, under a lock); make that first call outside any stream capture.
+ *   The address stays cached for the life of the process: after a
+ *   cudaDeviceReset of that device it is stale, so do not call this entry
+ *   point on a device that has been reset. All calls share the one array and it keeps the
  *   last call's contents; calls whose kernels overlap on the GPU (other
  *   streams, other host threads) race on it, so serialise them.
  * ------------------------------------------------------------------------- */

@@ -528,8 +528,50 @@ def relax(z: np.ndarray, zt: np.ndarray, has: np.ndarray, omega: float) -> np.nd
     return out
 
 
+# bfloat16: the IEEE binary32 layout cut to 16 bits (1 sign, 8 exponent and
+# 7 fraction bits), so 8 significant bits and binary32's exponent range.
+BF16_SIGNIFICANT_BITS = 8
+BF16_MIN_NORMAL_EXP = -126
+
+
+def round_bf16(x: np.ndarray) -> np.ndarray:
+    """Rounds float64 values to the nearest bfloat16 value, ties to the one
+    with an even last significand bit (IEEE round-to-nearest-even), and
+    returns them as float64 (exactly). A value with binary exponent E (that
+    is, in [2^E, 2^(E+1))) is a multiple of 2^(E-7) in bfloat16; below the
+    smallest normal 2^-126 the spacing stays 2^-133. numpy's ``rint`` rounds
+    halves to even, and scaling by powers of two is exact, so every step
+    here is exact but the one rounding. Values beyond bfloat16's range are
+    not expected (the embeddings are convex combinations of the input)."""
+    x = np.asarray(x, dtype=np.float64)
+    out = np.zeros_like(x)
+    nz = x != 0
+    _, e = np.frexp(x[nz])                      # |x| = f * 2^e, 0.5 <= f < 1
+    exp = np.maximum(e - 1, BF16_MIN_NORMAL_EXP)
+    q = np.ldexp(1.0, exp - (BF16_SIGNIFICANT_BITS - 1))
+    out[nz] = np.rint(x[nz] / q) * q
+    return out
+
+
+STORAGE_F64 = None
+STORAGE_BF16 = "bf16"
+
+
+def _store(z: np.ndarray, storage) -> np.ndarray:
+    """The rows as they are stored between half-sweeps: unchanged, or
+    rounded to bfloat16 (the library's BF16 storage keeps rows in bfloat16
+    and does its arithmetic in float32; the oracle does its arithmetic in
+    float64 and rounds each stored value once)."""
+    if storage is None:
+        return z
+    if storage == STORAGE_BF16:
+        return round_bf16(z)
+    raise ValueError("unknown storage %r" % (storage,))
+
+
 def refine(lv: Level, z_v: np.ndarray, z_e: np.ndarray, omega: float,
-           sweeps: int, mode: int = SWEEP_TWO_PHASE) -> Tuple[np.ndarray, np.ndarray]:
+           sweeps: int, mode: int = SWEEP_TWO_PHASE, storage=None
+           ) -> Tuple[np.ndarray, np.ndarray]:
     """Algorithm 2: ``sweeps`` iterations of smoothing plus relaxation over
     the star expansion of one level.
 
@@ -538,7 +580,10 @@ def refine(lv: Level, z_v: np.ndarray, z_e: np.ndarray, omega: float,
     embeddings are updated from the nodes and node embeddings from the
     hyperedges, and frames the scheme as SOR. The default
     ``SWEEP_TWO_PHASE`` updates all hyperedges from the current nodes, then
-    all nodes from the new hyperedges; both are provided."""
+    all nodes from the new hyperedges; both are provided.
+
+    ``storage=STORAGE_BF16`` rounds every relaxed row to bfloat16 as it is
+    stored (see ``_store``); the input rows must then be bfloat16 values."""
     z_v = np.array(z_v, dtype=np.float64)
     z_e = np.array(z_e, dtype=np.float64)
     He, Hv = incidence_matrices(lv)
@@ -546,14 +591,14 @@ def refine(lv: Level, z_v: np.ndarray, z_e: np.ndarray, omega: float,
     for _ in range(sweeps):
         if mode == SWEEP_TWO_PHASE:
             zt_e, has_e = smooth_edges(lv, He, z_v)
-            z_e = relax(z_e, zt_e, has_e, omega)
+            z_e = _store(relax(z_e, zt_e, has_e, omega), storage)
             zt_v, has_v = smooth_nodes(lv, Hv, deg, z_e)
-            z_v = relax(z_v, zt_v, has_v, omega)
+            z_v = _store(relax(z_v, zt_v, has_v, omega), storage)
         elif mode == SWEEP_JACOBI:
             zt_e, has_e = smooth_edges(lv, He, z_v)
             zt_v, has_v = smooth_nodes(lv, Hv, deg, z_e)
-            z_e = relax(z_e, zt_e, has_e, omega)
-            z_v = relax(z_v, zt_v, has_v, omega)
+            z_e = _store(relax(z_e, zt_e, has_e, omega), storage)
+            z_v = _store(relax(z_v, zt_v, has_v, omega), storage)
         else:
             raise ValueError("unknown sweep mode")
     return z_v, z_e
@@ -593,23 +638,25 @@ class VCycleResult:
 
 
 def vcycle(h: Hierarchy, z_coarsest: np.ndarray, omega: float, sweeps: int,
-           mode: int = SWEEP_TWO_PHASE, keep_levels: bool = False) -> VCycleResult:
+           mode: int = SWEEP_TWO_PHASE, keep_levels: bool = False,
+           storage=None) -> VCycleResult:
     """Refine the coarsest level from its initial embedding, then for every
     finer level project and refine, down to the original hypergraph
     (Section 3 overview, Fig. 1). ``z_coarsest`` holds the coarsest nodes'
-    rows first, then its hyperedges'."""
+    rows first, then its hyperedges'. ``storage`` is passed to ``refine``
+    (projection copies stored rows, so it needs no rounding of its own)."""
     L = len(h.levels) - 1
     top = h.levels[L]
     z = np.asarray(z_coarsest, dtype=np.float64)
     if z.shape[0] != top.n + top.m:
         raise ValueError("z_coarsest must have n_L + m_L rows")
-    z_v, z_e = refine(top, z[:top.n], z[top.n:], omega, sweeps, mode)
+    z_v, z_e = refine(top, z[:top.n], z[top.n:], omega, sweeps, mode, storage)
     per = [None] * (L + 1)
     if keep_levels:
         per[L] = (z_v, z_e)
     for ell in range(L - 1, -1, -1):
         z_v, z_e = project(h.rep_v[ell], h.rep_e[ell], z_v, z_e)
-        z_v, z_e = refine(h.levels[ell], z_v, z_e, omega, sweeps, mode)
+        z_v, z_e = refine(h.levels[ell], z_v, z_e, omega, sweeps, mode, storage)
         if keep_levels:
             per[ell] = (z_v, z_e)
     return VCycleResult(z_v=z_v, z_e=z_e, per_level=per)

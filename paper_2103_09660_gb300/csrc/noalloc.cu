@@ -32,7 +32,9 @@ std::mutex g_mu;
 float* g_scratch_dev[kMaxDevices] = {nullptr};
 
 // Device address of g_noalloc_scratch on `device` (which must be current).
-// The first call on a device looks it up; later calls reuse it.
+// The first call on a device looks it up; later calls reuse it. A
+// cudaDeviceReset unloads the module and makes the cached address stale,
+// which is why the header rules out calls on a device that has been reset.
 int scratch_address(int device, float** out) {
   if (device < 0 || device >= kMaxDevices)
     HNV_FAIL(HNV_ERR_INVALID_ARG, "device %d out of range for the static scratch table", device);

@@ -4,6 +4,10 @@
   against the oracle's.
 * One two-phase sweep of every level from the same seeded float32 rows,
   compared with the oracle's float64 sweep on every row.
+* The whole V-cycle (20 sweeps on each of the 5 levels, d = 128) element by
+  element against the oracle's float64 V-cycle on every level, the oracle
+  run over column blocks in worker processes; hnv_vcycle's output equals
+  the level-by-level result bit for bit.
 * Properties of the full V-cycle at this size: a constant embedding is a
   fixed point of projection and refinement, and two runs are bitwise equal.
 """
@@ -14,7 +18,8 @@ import pytest
 import hypergen
 from oracle import hnv_oracle as O
 
-from _helpers import FP32_TOL, assert_hierarchy_equal, oracle_level0, rel_err
+from _helpers import (FP32_TOL, assert_bf16_close, assert_hierarchy_equal, bf16_errors,
+                      oracle_level0, oracle_vcycle_columns, rel_err)
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
@@ -56,6 +61,31 @@ def test_fullsize_hierarchy_and_one_sweep_per_level(H, workload):
             assert ev < FP32_TOL and ee < FP32_TOL, (ell, ev, ee)
 
 
+def test_fullsize_vcycle_against_fp64_oracle(H, workload, tmp_path):
+    """The V-cycle bench.py times, compared on every element of every level."""
+    import torch
+    spec, hg, h = workload
+    top = h.levels[-1]
+    zc = hypergen.coarsest_embedding(top.n + top.m, spec.d, seed=spec.seed)
+    with H.Graph.from_hypergraph(hg, on_device=True) as G:
+        G.coarsen(min_nodes=spec.min_nodes, max_levels=spec.max_levels, seed=spec.seed)
+        zcd = torch.from_numpy(zc).cuda()
+        per = _levels_on_gpu(H, G, zcd, spec.sweeps)
+        zv = torch.empty((hg.n, spec.d), device="cuda")
+        ze = torch.empty((hg.m, spec.d), device="cuda")
+        G.vcycle(zcd, zv, ze, 0.5, spec.sweeps)
+        G.sync_status()
+        assert torch.equal(torch.cat([zv, ze]), per[0])
+        got = [p.cpu() for p in per]
+        del per, zv, ze
+    ref = oracle_vcycle_columns(h, zc, 0.5, spec.sweeps, str(tmp_path))
+    for l in range(len(h.levels)):
+        r = ref(l)
+        err = rel_err(got[l].double().numpy(), r)
+        print("level %d: rows %d, max row-relative error %.2e" % (l, r.shape[0], err))
+        assert err < FP32_TOL, (l, err)
+
+
 def test_fullsize_vcycle_properties(H, workload):
     import torch
     spec, hg, h = workload
@@ -91,12 +121,14 @@ def test_fullsize_vcycle_properties(H, workload):
 
 def _oracle_vcycle_cols(args):
     """Oracle V-cycle of a block of embedding columns (refinement treats every
-    column independently, so column blocks are independent computations)."""
+    column independently, so column blocks are independent computations),
+    exact and with bfloat16 storage."""
     arrays, params, zc_block, sweeps = args
     n, m, ptr, nodes, w = arrays
     h = O.coarsen(O.build_level(n, m, ptr, nodes, w), O.CoarsenParams(**params))
     res = O.vcycle(h, zc_block, 0.5, sweeps, keep_levels=True)
-    return [np.vstack(p) for p in res.per_level]
+    r16 = O.vcycle(h, zc_block, 0.5, sweeps, keep_levels=True, storage=O.STORAGE_BF16)
+    return [np.vstack(p) for p in res.per_level], [np.vstack(p) for p in r16.per_level]
 
 
 def _levels_on_gpu(H, G, zc, sweeps):
@@ -143,12 +175,17 @@ def test_fullsize_bf16_subsample_against_fp64(H):
                                                     spec.sweeps) for c in cols])
         M = float(zc.abs().max())
         for l in range(L):
-            ref = torch.from_numpy(np.hstack([p[l] for p in parts])).cuda()
+            ref = torch.from_numpy(np.hstack([p[0][l] for p in parts])).cuda()
+            ref16 = np.hstack([p[1][l] for p in parts])
             e32 = float((z32[l].double() - ref).abs().max()) / M
             e16 = float((z16[l].double() - ref).abs().max()) / M
+            got16 = z16[l].double().cpu().numpy()
+            p_max, p_rms = bf16_errors(got16, ref16)
             half_sweeps = 2 * spec.sweeps * (L - l)           # along the path to level l
-            print("level %d: fp32 %.2e  bf16 %.4f (bar %.3f)" % (l, e32, e16, half_sweeps * 2.0 ** -8))
+            print("level %d: fp32 %.2e  bf16 vs fp64 %.4f (bar %.3f)  bf16 vs bf16-storage "
+                  "oracle: max %.2e rms %.2e" % (l, e32, e16, half_sweeps * 2.0 ** -8, p_max, p_rms))
             assert e32 < 1e-5
+            assert_bf16_close(got16, ref16, ("level", l))
             assert e16 <= half_sweeps * 2.0 ** -8
 
 

@@ -176,3 +176,63 @@ def test_refine_until_rules():
     d = O.refine_until(lv, zv, ze, 0.5, 400, 1e-3)
     assert d[2] < 400 and d[3][-1] <= 1e-3 < d[3][-2]
     assert d[3][-1] < d[3][0] / 100
+
+
+def _cosines_f64(lv, X):
+    """Every incidence's cosine (CSC order) computed in float64 from the
+    level's features: member means, dot products and norms (0 where a norm
+    is 0, the oracle's reading)."""
+    X64 = np.asarray(X, dtype=np.float64)
+    size = np.diff(lv.e_ptr)
+    FE = np.zeros((lv.m, X64.shape[1]))
+    nz = size > 0
+    FE[nz] = np.add.reduceat(X64[lv.e_nodes], lv.e_ptr[:-1][nz], axis=0) / size[nz, None]
+    node_of = O.row_of(lv.v_ptr)
+    edge = lv.v_edges
+    dot = np.einsum("ij,ij->i", FE[edge], X64[node_of])
+    den = np.linalg.norm(FE, axis=1)[edge] * np.linalg.norm(X64, axis=1)[node_of]
+    return np.where(den > 0, dot / np.where(den > 0, den, 1.0), 0.0), node_of, edge
+
+
+def test_chosen_hyperedge_is_optimal_in_float64_at_50k():
+    """The float32 feature rule on the 50,000-node graph of the GPU feature
+    tests (4 levels), checked against float64 cosines at every level: each
+    choice scores within 1e-5 of its node's float64 best, and a node whose
+    float64 best beats its runner-up by more than 1e-4 gets that best.
+    The GPU is checked bit for bit against these float32 choices."""
+    hg = hypergen.planted_hypergraph(50_000, 40_000, C=16, alpha=1.8, cap=5000, p_in=0.7,
+                                     weighted=True, seed=7)
+    X = hypergen.planted_features(hg, 24, sigma=1.0, seed=7)
+    params = O.CoarsenParams(policy=O.ASSIGN_COSINE, min_nodes=500, max_levels=4, features=X)
+    h = O.coarsen(oracle_level0(hg), params)
+    assert len(h.levels) >= 3
+    clear_total = 0
+    for ell, lv in enumerate(h.levels[:-1]):
+        Xl = h.features[ell]
+        prio = O.hash_priority(np.arange(lv.m, dtype=np.uint64), params.seed, ell)
+        c = O.assign_cosine(lv, Xl, prio)
+        cos, node_of, edge = _cosines_f64(lv, Xl)
+        # float64 best and runner-up per node (nodes with hyperedges)
+        order = np.lexsort((-cos, node_of))
+        start = lv.v_ptr[:-1]
+        deg = np.diff(lv.v_ptr)
+        has = deg > 0
+        best = np.full(lv.n, -np.inf)
+        best[has] = cos[order[start[has]]]
+        second = np.full(lv.n, -np.inf)
+        two = deg > 1
+        second[two] = cos[order[start[two] + 1]]
+        best_edge = np.full(lv.n, -1)
+        best_edge[has] = edge[order[start[has]]]
+        # the float64 cosine of each node's chosen hyperedge
+        key = node_of * (lv.m + 1) + edge
+        chosen_key = np.arange(lv.n) * (lv.m + 1) + c
+        at = np.searchsorted(key, chosen_key[has])    # CSC keys ascend (node, edge)
+        assert np.all(key[at] == chosen_key[has])
+        got = cos[at]
+        assert np.all(got >= best[has] - 1e-5), (ell, float((best[has] - got).max()))
+        clear = has & (best - second > 1e-4)
+        assert np.all(c[clear] == best_edge[clear]), ell
+        assert np.all(c[~has] == -1)
+        clear_total += int(clear.sum())
+    assert clear_total > 10_000      # the margin rule decides most choices

@@ -76,35 +76,61 @@ def test_noalloc_matches_allocating_refine_twice(H, d):
                 assert rel_err(ze.double().cpu().numpy(), ref_e.double().cpu().numpy()) < FP32_TOL
 
 
+def _install_counting_allocator(H, calls):
+    """A device allocator hook that records every request and grants none
+    (it returns NULL, so an allocating call fails with HNV_ERR_OOM)."""
+    AF = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+    FF = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+    fail_alloc = AF(lambda nbytes, s, ctx: calls.append(nbytes))
+    no_free = FF(lambda p, s, ctx: calls.append(-1))
+    assert H.lib().hnv_set_allocator(ctypes.cast(fail_alloc, ctypes.c_void_p),
+                                     ctypes.cast(no_free, ctypes.c_void_p), None) == 0
+    return fail_alloc, no_free          # keep the callbacks alive while installed
+
+
 def test_noalloc_requests_no_allocation(H):
+    """On a graph that has never refined (so it holds no split-row scratch),
+    the no-allocation entry point runs with an allocator hook that refuses
+    everything; as a positive control, hnv_refine on a second such graph does
+    ask that hook for memory. The reference rows come from the second graph
+    after the hook is removed."""
     import torch
     hg = _skewed_hypergraph(2)
-    with H.Graph.from_hypergraph(hg) as G:
+    L = H.lib()
+    with H.Graph.from_hypergraph(hg) as G, H.Graph.from_hypergraph(hg) as G2:
         n, m, _ = G.level_info(0)
         z = torch.from_numpy(np.random.default_rng(0).standard_normal(
             (n + m, 64)).astype(np.float32)).cuda()
-        ref_v, ref_e = z[:n].clone(), z[n:].clone()
-        G.refine(0, ref_v, ref_e, 0.5, 2)
-        calls = []
-        AF = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
-        FF = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
-        fail_alloc = AF(lambda nbytes, s, ctx: calls.append(nbytes))
-        no_free = FF(lambda p, s, ctx: calls.append(-1))
-        L = H.lib()
+        zv, ze = z[:n].clone(), z[n:].clone()
+        rv, re_ = z[:n].clone(), z[n:].clone()
         torch.cuda.synchronize()
-        assert L.hnv_set_allocator(ctypes.cast(fail_alloc, ctypes.c_void_p),
-                                   ctypes.cast(no_free, ctypes.c_void_p), None) == 0
+
+        calls = []
+        keep = _install_counting_allocator(H, calls)
         try:
-            zv, ze = z[:n].clone(), z[n:].clone()
-            torch.cuda.synchronize()
             rc = _call_noalloc(H, G, 0, zv, ze, 0.5, 2)
             torch.cuda.synchronize()
         finally:
             assert L.hnv_set_allocator(None, None, None) == 0
         assert rc == 0, L.hnv_last_error_detail()
         assert calls == []
-        assert rel_err(zv.double().cpu().numpy(), ref_v.double().cpu().numpy()) < FP32_TOL
-        assert rel_err(ze.double().cpu().numpy(), ref_e.double().cpu().numpy()) < FP32_TOL
+
+        control = []
+        keep = _install_counting_allocator(H, control)
+        try:
+            rc2 = L.hnv_refine(G2.handle, 0, rv.data_ptr(), re_.data_ptr(), H.F32, 64, 0.5, 2,
+                               H.SWEEP_TWO_PHASE, H._stream_handle(G2.stream))
+            torch.cuda.synchronize()
+        finally:
+            assert L.hnv_set_allocator(None, None, None) == 0
+        del keep
+        assert rc2 == -4, rc2                    # HNV_ERR_OOM: the hook refused
+        assert any(c > 0 for c in control)       # hnv_refine did ask for memory
+
+        G2.refine(0, rv, re_, 0.5, 2)            # reference, allocator restored
+        torch.cuda.synchronize()
+        assert rel_err(zv.double().cpu().numpy(), rv.double().cpu().numpy()) < FP32_TOL
+        assert rel_err(ze.double().cpu().numpy(), re_.double().cpu().numpy()) < FP32_TOL
 
 
 def test_noalloc_refuses_levels_beyond_the_scratch(H):
