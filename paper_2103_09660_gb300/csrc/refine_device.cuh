@@ -62,14 +62,16 @@ struct VecT<__nv_bfloat16> {
 //   chunk:     partials[slot] = sum_k wgt_k src[idx_k]   (float32)
 // norm (inv_norm) may be null (1); with keep == 0 the own row is not read.
 // PRE: the caller supplies this lane's first neighbour index (incidence
-// beg + lg, any value where lg >= len) in idx0 instead of it being loaded.
+// beg + lg, any value where lg >= len) in idx0 instead of it being loaded,
+// and for a weighted side that incidence's weight in w0.
 template <typename T, int G, int VPL, bool WEIGHTED, bool PRE = false>
 __device__ __forceinline__ void gather_item(int4 it, int lg, const int32_t* __restrict__ idx,
                                             const float* __restrict__ inc_w,
                                             const float* __restrict__ inv_norm,
                                             const uint4* __restrict__ src, const uint4* self_in,
                                             uint4* out, int32_t dv, float keep, float scale,
-                                            float* __restrict__ partials, int32_t idx0 = 0) {
+                                            float* __restrict__ partials, int32_t idx0 = 0,
+                                            float w0 = 0.f) {
   using V = VecT<T>;
   constexpr int N = V::N;
   // row loads in flight per lane (the weighted variant also holds a weight
@@ -105,7 +107,7 @@ __device__ __forceinline__ void gather_item(int4 it, int lg, const int32_t* __re
       const int32_t my_idx =
           have ? ((PRE && off == 0) ? idx0 : __ldg(idx + beg + off + lg)) : 0;
       float my_w = 0.f;
-      if (WEIGHTED) my_w = have ? __ldg(inc_w + beg + off + lg) : 0.f;
+      if (WEIGHTED) my_w = have ? ((PRE && off == 0) ? w0 : __ldg(inc_w + beg + off + lg)) : 0.f;
       const int32_t cnt = min(G, maxlen - off);
       for (int32_t t = 0; t < cnt; t += U) {
         uint4 x[U][VPL];
