@@ -22,8 +22,10 @@
  *    4 <= d <= 1024.
  *  - The hierarchy (all levels' incidence arrays and maps) is owned by an
  *    opaque hnv_graph and released by hnv_graph_free(). Its device memory
- *    is allocated stream-ordered (cudaMallocAsync) unless an allocator is
- *    installed with hnv_set_allocator().
+ *    is allocated stream-ordered from a memory pool of the library's own
+ *    (one per device, keeping freed memory for reuse; see
+ *    hnv_release_cached_memory) unless an allocator is installed with
+ *    hnv_set_allocator().
  *  - IDs are int32: n, m < 2^31 and every level's incidence count
  *    nnz < 2^31 (HNV_ERR_TOO_LARGE otherwise).
  *  - One graph (or one batch) holds scratch that its calls share (split-row
@@ -337,18 +339,32 @@ int hnv_vcycle_backward(hnv_graph* g, const float* checkpoints, const float* g_v
  * first) every graph whose coarsest level is >= s projects onto its level s
  * (or starts from its input rows at its coarsest level) and runs the
  * two-phase sweeps of Algorithm 2 there. Per half-sweep, one launch per row
- * class covers the rows of all graphs (a work list with a graph index per
- * item); the whole V-cycle can be captured once into a CUDA graph and
- * replayed. Results equal hnv_vcycle on each graph (same per-row sums).
+ * class (or one persistent launch) covers the rows of all graphs (a work
+ * list with a graph index per item); the whole V-cycle can be captured once
+ * into a CUDA graph and replayed. Results equal hnv_vcycle on each graph
+ * (same per-row sums). The persistent launches use a small array of task
+ * counters owned by the batch (one per half-sweep), cleared at the start of
+ * every V-cycle; V-cycles of one batch must not overlap on the GPU.
  * ------------------------------------------------------------------------- */
 typedef struct hnv_batch hnv_batch;
 
-/* Row-length classes and lanes per row chosen by hnv_batch_autotune. */
+/* Half-sweep kernels of the batched V-cycle. PER_CLASS: one launch per row
+ * class (rows of 1..a_max, a_max+1..b_max and longer rows with chunks), the
+ * classes on concurrent streams. PERSISTENT: one launch per half-sweep over
+ * every item of every class and graph; resident warps take fixed-size tasks
+ * from a counter in device memory, the longest items first. Both are followed
+ * by the split-row reduction and give the same bits. */
+enum { HNV_BATCH_KERNEL_PER_CLASS = 0, HNV_BATCH_KERNEL_PERSISTENT = 1 };
+
+/* Row-length classes, lanes per row and half-sweep kernel chosen by
+ * hnv_batch_autotune. */
 typedef struct {
   int32_t a_max, b_max, c_max;          /* class boundaries (incidences) */
   int32_t lanes_a, lanes_b, lanes_rest; /* lanes per row of the classes  */
-  float best_ms;                        /* one level-0 sweep, ms (-1: cached) */
+  float best_ms;                        /* V-cycle, 1 sweep per level, ms (-1: cached) */
   int32_t from_cache;                   /* 1: taken from the tuning cache */
+  int32_t kernel;                       /* HNV_BATCH_KERNEL_*              */
+  float persistent_ms;                  /* the same with the persistent kernel (-1: cached) */
 } hnv_batch_tuning;
 
 /* A batch over `count` graphs (built and coarsened; all on one device). The
@@ -368,10 +384,20 @@ int hnv_batch_create(hnv_graph* const* graphs, int32_t count, hnv_batch** out);
 int hnv_batch_offsets(const hnv_batch* b, int64_t* coarsest_rows, int64_t* node_rows,
                       int64_t* edge_rows);
 
-/* Times candidate row-class boundaries and lanes per row on one level-0 sweep
- * of the batch and keeps the fastest (cached per dtype, d and the batch's
- * level-0 row-length histogram). Synchronises. */
+/* Times candidate row-class boundaries and lanes per row of the per-class
+ * kernel, and the persistent kernel, on a whole V-cycle of the batch with one
+ * sweep per level, and keeps the fastest (cached per dtype, d and the batch's
+ * level-0 row-length histogram). Uses scratch rows of the batch's level-0
+ * size while it runs. Synchronises. */
 int hnv_batch_autotune(hnv_batch* b, hnv_dtype dt, int d, float omega, hnv_batch_tuning* chosen);
+
+/* Selects the half-sweep kernel (HNV_BATCH_KERNEL_*) of later hnv_batch_vcycle
+ * calls; a new batch starts with HNV_BATCH_KERNEL_PER_CLASS (measured faster
+ * on the 256-graph batching workload), and hnv_batch_autotune sets the faster. Errors: HNV_ERR_INVALID_ARG (NULL batch,
+ * unknown kernel). hnv_batch_get_kernel returns the current one (or
+ * HNV_ERR_INVALID_ARG for NULL). */
+int hnv_batch_set_kernel(hnv_batch* b, int kernel);
+int hnv_batch_get_kernel(const hnv_batch* b);
 
 /* The two-phase V-cycle of every graph of the batch (device buffers laid out
  * as hnv_batch_offsets says; d % 8 == 0). With use_cuda_graph the whole
@@ -401,6 +427,16 @@ void hnv_batch_free(hnv_batch* b);
  * HNV_ERR_CUDA for a CUDA error, else HNV_OK. Clears the recorded failure. */
 int hnv_sync_status(hnv_graph* g, hnv_stream_t stream);
 
+/* Self-test of the device-side failure path (a library service; the paper
+ * has no counterpart). Launches one bounded wait, the kind the TMA gather
+ * kernels use, on an mbarrier that nothing completes (no memory copy is in
+ * flight); after limit_us microseconds (1 .. 1000000) the wait gives up and
+ * records a timeout for the graph, exactly as a refinement kernel would.
+ * The next hnv_sync_status on that graph returns HNV_ERR_TIMEOUT (and
+ * clears it); the context stays usable. Asynchronous on stream.
+ * Errors: HNV_ERR_INVALID_ARG (NULL graph, limit out of range), HNV_ERR_CUDA. */
+int hnv_selftest_wait_timeout(hnv_graph* g, uint32_t limit_us, hnv_stream_t stream);
+
 /* Releases the hierarchy (stream-ordered on the graph's stream). NULL is a no-op. */
 void hnv_graph_free(hnv_graph* g);
 
@@ -411,12 +447,20 @@ const char* hnv_error_string(int code);
 /* One-line detail of the calling thread's last error ("" if none). */
 const char* hnv_last_error_detail(void);
 
-/* Replaces the device allocator (NULL, NULL restores cudaMallocAsync /
- * cudaFreeAsync). alloc returns NULL on failure, which the library reports
- * as HNV_ERR_OOM. Not thread-safe with respect to calls in flight. */
+/* Replaces the device allocator (NULL, NULL restores the library's pool:
+ * cudaMallocFromPoolAsync / cudaFreeAsync). alloc returns NULL on failure,
+ * which the library reports as HNV_ERR_OOM. Not thread-safe with respect to
+ * calls in flight. */
 typedef void* (*hnv_alloc_fn)(size_t bytes, hnv_stream_t stream, void* ctx);
 typedef void (*hnv_free_fn)(void* ptr, hnv_stream_t stream, void* ctx);
 int hnv_set_allocator(hnv_alloc_fn alloc_fn, hnv_free_fn free_fn, void* ctx);
+
+/* The library allocates from a stream-ordered memory pool of its own per
+ * device whose freed memory stays mapped for the next call (a V-cycle step
+ * at the 1M-node size allocates and frees about 1.5 GB; mapping it afresh on
+ * every call costs time). This returns the pools' unused memory to the
+ * system (memory still allocated stays). Errors: HNV_ERR_CUDA. */
+int hnv_release_cached_memory(void);
 
 /* Number of kernels this library has launched in the process so far. */
 int64_t hnv_kernel_launch_count(void);

@@ -23,7 +23,8 @@ import numpy as np
 __all__ = [
     "HNVError", "HNVLibraryMissing", "lib", "library_path",
     "ASSIGN_HASH", "ASSIGN_LOW_DEGREE", "ASSIGN_HIGH_WEIGHT", "ASSIGN_EXPLICIT",
-    "SWEEP_TWO_PHASE", "SWEEP_JACOBI", "F32", "BF16",
+    "SWEEP_TWO_PHASE", "SWEEP_JACOBI", "F32", "BF16", "BATCH_KERNEL_PER_CLASS",
+    "BATCH_KERNEL_PERSISTENT",
     "ARR_E_PTR", "ARR_E_NODES", "ARR_V_PTR", "ARR_V_EDGES", "ARR_W", "ARR_REP_V",
     "ARR_REP_E", "ARR_DEG_V",
     "PHASE_BUILD", "PHASE_COARSEN", "PHASE_PROJECT", "PHASE_REFINE_E", "PHASE_REFINE_V",
@@ -40,6 +41,7 @@ library_path = os.path.join(_HERE, "libhnv.so")
 ASSIGN_HASH, ASSIGN_LOW_DEGREE, ASSIGN_HIGH_WEIGHT, ASSIGN_EXPLICIT, ASSIGN_COSINE = 0, 1, 2, 3, 4
 SWEEP_TWO_PHASE, SWEEP_JACOBI = 0, 1
 F32, BF16 = 0, 1
+BATCH_KERNEL_PER_CLASS, BATCH_KERNEL_PERSISTENT = 0, 1
 (ARR_E_PTR, ARR_E_NODES, ARR_V_PTR, ARR_V_EDGES, ARR_W, ARR_REP_V, ARR_REP_E,
  ARR_DEG_V) = range(8)
 PHASE_BUILD, PHASE_COARSEN, PHASE_PROJECT, PHASE_REFINE_E, PHASE_REFINE_V = range(5)
@@ -71,7 +73,8 @@ class BatchTuning(ctypes.Structure):
     _fields_ = [("a_max", ctypes.c_int32), ("b_max", ctypes.c_int32), ("c_max", ctypes.c_int32),
                 ("lanes_a", ctypes.c_int32), ("lanes_b", ctypes.c_int32),
                 ("lanes_rest", ctypes.c_int32), ("best_ms", ctypes.c_float),
-                ("from_cache", ctypes.c_int32)]
+                ("from_cache", ctypes.c_int32), ("kernel", ctypes.c_int32),
+                ("persistent_ms", ctypes.c_float)]
 
 
 _lib = None
@@ -105,6 +108,10 @@ def _declare(L):
         "hnv_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, f32, ctypes.POINTER(BatchTuning)]),
         "hnv_batch_vcycle": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_int, f32, ctypes.c_int, ctypes.c_int, _P]),
         "hnv_batch_free": (None, [_P]),
+        "hnv_batch_set_kernel": (ctypes.c_int, [_P, ctypes.c_int]),
+        "hnv_release_cached_memory": (ctypes.c_int, []),
+        "hnv_selftest_wait_timeout": (ctypes.c_int, [_P, ctypes.c_uint32, _P]),
+        "hnv_batch_get_kernel": (ctypes.c_int, [_P]),
         "hnv_set_weights": (ctypes.c_int, [_P, _P, ctypes.c_int, _P]),
         "hnv_checkpoint_floats": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(i64)]),
         "hnv_vcycle_save": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, f32, ctypes.c_int, _P, _P]),
@@ -534,8 +541,9 @@ class Graph:
 
 class Batch:
     """Many hypergraphs refined together (hnv_batch_*): one launch per row
-    class and half-sweep covers every graph, the V-cycle is captured into a
-    CUDA graph. The graphs must stay alive while the batch is used."""
+    class (or one persistent launch) per half-sweep covers every graph, the
+    V-cycle is captured into a CUDA graph. The graphs must stay alive while
+    the batch is used."""
 
     def __init__(self, graphs):
         self.graphs = list(graphs)
@@ -559,6 +567,17 @@ class Batch:
         _check(lib().hnv_batch_autotune(self.handle, dtype, int(d), float(omega), ctypes.byref(t)),
                "hnv_batch_autotune")
         return {f: getattr(t, f) for f, _ in BatchTuning._fields_}
+
+    @property
+    def kernel(self) -> int:
+        """The half-sweep kernel (BATCH_KERNEL_PER_CLASS or BATCH_KERNEL_PERSISTENT)."""
+        k = lib().hnv_batch_get_kernel(self.handle)
+        _check(min(k, 0), "hnv_batch_get_kernel")
+        return k
+
+    @kernel.setter
+    def kernel(self, k: int):
+        _check(lib().hnv_batch_set_kernel(self.handle, int(k)), "hnv_batch_set_kernel")
 
     def vcycle(self, z_coarsest, z_v_out, z_e_out, omega=0.5, sweeps=10, use_cuda_graph=True):
         dt, tdt = _emb_dtype(z_coarsest)

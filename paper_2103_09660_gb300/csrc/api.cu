@@ -101,6 +101,7 @@ void drop_maps(Level* lv, cudaStream_t s) {
 int vcycle_impl(hnv_graph* g, const void* z_coarsest, void* z_v_out, void* z_e_out, int dtype,
                 int d, float omega, int sweeps, int mode, int on_device, cudaStream_t s,
                 float* ckpt = nullptr) {
+  NvtxRange nvtx("hnv vcycle (%d levels)", (int)g->levels.size());
   const int L = (int)g->levels.size() - 1;
   const size_t row_bytes = dtype_size((hnv_dtype)dtype) * (size_t)d;
   TempPool pool(s);
@@ -171,6 +172,7 @@ extern "C" {
 int hnv_build_incidence(int32_t n_nodes, int32_t n_edges, const int64_t* edge_ptr,
                         const int32_t* edge_nodes, const float* edge_w, int inputs_on_device,
                         hnv_stream_t stream, hnv_graph** out) {
+  NvtxRange nvtx("hnv build incidence");
   clear_error_detail();
   if (!out) HNV_FAIL(HNV_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
@@ -617,6 +619,16 @@ int hnv_sync_status(hnv_graph* g, hnv_stream_t stream) {
   if (bits & ERRBIT_BAD_ITEM)
     HNV_FAIL(HNV_ERR_STATE, "a batched work item lay outside its graph's arrays and was skipped");
   return HNV_OK;
+}
+
+int hnv_selftest_wait_timeout(hnv_graph* g, uint32_t limit_us, hnv_stream_t stream) {
+  clear_error_detail();
+  if (!g) HNV_FAIL(HNV_ERR_INVALID_ARG, "graph is NULL");
+  if (limit_us < 1 || limit_us > 1000000)
+    HNV_FAIL(HNV_ERR_INVALID_ARG, "limit_us = %u: need 1 .. 1000000", limit_us);
+  DeviceGuard dgd(g->device);
+  return wait_selftest(g->d_err, (uint64_t)limit_us * 1000ull,
+                       reinterpret_cast<cudaStream_t>(stream));
 }
 
 void hnv_graph_free(hnv_graph* g) {

@@ -13,9 +13,17 @@
 // whole V-cycle (all steps, sweeps, projections) is captured once into a
 // CUDA graph and replayed.
 //
+// Two half-sweep kernels: one launch per row class (classes on concurrent
+// streams, lanes per row chosen per class), or one persistent launch over
+// every item of the half-sweep (warps take tasks from a counter; see
+// batched_persistent_kernel). Both are followed by the split-row reduction.
+//
 // Autotuner: the row-class boundaries (PlanShape) and the lanes per row of
-// the short classes are chosen by timing candidate settings on the batch's
-// level 0, and cached per (dtype, d, level-0 length histogram).
+// the short classes of the per-class kernel, and the persistent kernel, are
+// timed on a whole V-cycle of the batch with one sweep per level (the coarse
+// levels dominate a batch of many small graphs, so a level-0 sweep alone
+// picks badly), and the fastest is kept and cached per (dtype, d, level-0
+// length histogram).
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
@@ -117,6 +125,97 @@ batched_gather_kernel(const int4* __restrict__ items, const int32_t* __restrict_
     }
     dev::gather_item<T, G, VPL, W>(it, lg, sd.idx, sd.inc_w, sd.inv_norm, sd.src, sd.self_in,
                                    sd.out, dv, keep, scale, sd.partials);
+  }
+}
+
+// Persistent half-sweep: one launch runs every item of one side of one step,
+// over all graphs and all row classes. A warp takes a task (kTaskPasses
+// passes over items of one class) from a counter in device memory until
+// none is left. The long rows and chunks (the last class) come first, then
+// class B, then class A, so the short rows fill the tail. Classes B and the
+// rest use one lane per 16-byte vector of the row (GL lanes); the rows of
+// class A (1..a_max incidences) use GA = GL/4 lanes with 4 vectors each, so
+// a warp has four times as many of these short rows in flight. The sums run
+// in the same order as in the per-class kernels: the results are the same
+// bits.
+constexpr int kTaskPasses = 8;
+constexpr int kPersistThreads = 64;
+constexpr int kCountersPerHalf = 1;   // task counters of one persistent launch
+
+template <typename T, int G, int VPL, bool W>
+__device__ __forceinline__ void persistent_task(const int4* __restrict__ items,
+                                                const int32_t* __restrict__ item_g,
+                                                int32_t lo, int32_t hi,
+                                                const GraphSide* __restrict__ sides,
+                                                int32_t n_graphs, int32_t dv, float keep,
+                                                float scale) {
+  constexpr int R = 32 / G;
+  const int lane = threadIdx.x & 31;
+  const int grp = lane / G;
+  const int lg = lane & (G - 1);
+#pragma unroll 1
+  for (int k = 0; k < kTaskPasses; ++k) {
+    const int32_t base = lo + k * R;
+    if (base >= hi) break;                                     // warp-uniform
+    const int32_t item = base + grp;
+    int4 it = make_int4(-1, 0, 0, -1);
+    int32_t gi = 0;
+    bool bad = false;
+    if (item < hi) {
+      it = __ldg(items + item);
+      gi = __ldg(item_g + item);
+      if (gi < 0 || gi >= n_graphs) {
+        gi = 0;
+        bad = true;
+      }
+    }
+    const GraphSide sd = sides[gi];
+    if (item < hi) {
+      bad = bad || it.x < -1 || it.x >= sd.self_rows || it.y < 0 || it.z < 0 ||
+            (int64_t)it.y + it.z > sd.nnz || it.w >= sd.n_slots || (it.x < 0 && it.w < 0);
+      if (bad) {
+        if (sd.err) atomicOr(sd.err, (int32_t)ERRBIT_BAD_ITEM);
+        it = make_int4(-1, 0, 0, -1);
+      }
+    }
+    dev::gather_item<T, G, VPL, W>(it, lg, sd.idx, sd.inc_w, sd.inv_norm, sd.src, sd.self_in,
+                                   sd.out, dv, keep, scale, sd.partials);
+  }
+}
+
+template <typename T, int GA, int VA, int GL, int VL, bool W>
+__global__ void __launch_bounds__(256)
+batched_persistent_kernel(const int4* __restrict__ items, const int32_t* __restrict__ item_g,
+                          int32_t n_a, int32_t n_b, int32_t n_rest,
+                          const GraphSide* __restrict__ sides, int32_t n_graphs, int32_t dv,
+                          float keep, float scale, int32_t* __restrict__ counter) {
+  constexpr int32_t kPerA = (32 / GA) * kTaskPasses;   // items per task
+  constexpr int32_t kPerL = (32 / GL) * kTaskPasses;
+  const int lane = threadIdx.x & 31;
+  // tasks: the rest (items [n_a + n_b, n)), then B, then A, each from its end
+  const int32_t t_rest = (int32_t)(((int64_t)n_rest + kPerL - 1) / kPerL);
+  const int32_t t_b = (int32_t)(((int64_t)n_b + kPerL - 1) / kPerL);
+  const int32_t t_a = (int32_t)(((int64_t)n_a + kPerA - 1) / kPerA);
+  const int32_t n_tasks = t_rest + t_b + t_a;
+  while (true) {
+    int32_t t = 0;
+    if (lane == 0) t = atomicAdd(counter, 1);
+    t = __shfl_sync(dev::kFull, t, 0);
+    if (t >= n_tasks) break;                                   // warp-uniform
+    if (t < t_rest + t_b) {
+      const bool rest = t < t_rest;
+      const int32_t base = rest ? n_a + n_b : n_a;             // the class's items
+      const int32_t end = rest ? n_a + n_b + n_rest : n_a + n_b;
+      const int32_t tt = rest ? t : t - t_rest;
+      const int32_t hi = end - tt * kPerL;
+      const int32_t lo = hi - kPerL > base ? hi - kPerL : base;
+      persistent_task<T, GL, VL, W>(items, item_g, lo, hi, sides, n_graphs, dv, keep, scale);
+    } else {
+      const int32_t tt = t - t_rest - t_b;
+      const int32_t hi = n_a - tt * kPerA;
+      const int32_t lo = hi - kPerA > 0 ? hi - kPerA : 0;
+      persistent_task<T, GA, VA, W>(items, item_g, lo, hi, sides, n_graphs, dv, keep, scale);
+    }
   }
 }
 
@@ -267,6 +366,12 @@ struct hnv_batch {
   float exec_omega = -1.f;
   int exec_sweeps = -1;
   int64_t exec_kernels = 0;        // kernel nodes of the captured V-cycle
+  int exec_kernel = -1;            // the half-sweep kernel it was captured with
+  // half-sweep kernel: 0 one launch per row class, 1 one persistent launch
+  int kernel = HNV_BATCH_KERNEL_PER_CLASS;
+  // task counters of the persistent launches, one per half-sweep of a V-cycle
+  int32_t* counters = nullptr;
+  int64_t counters_n = 0;
   std::vector<int64_t> coarse_off, v_off, e_off;   // row offsets (count + 1)
 };
 
@@ -580,9 +685,58 @@ int launch_batched_dispatch(int G, int VPL, const BSide& B, int64_t first, int32
 // classes B and the rest run on the batch's side streams, forked from s and
 // joined back (inside a capture these become parallel branches of the
 // graph); the split-row reduction follows the last class on its stream.
+template <typename T, int GA, int VA, int GL, int VL, bool W>
+int launch_persistent(const BSide& B, int dv, float keep, float scale, int32_t* counter,
+                      cudaStream_t s) {
+  const int32_t n = B.n_cls[0] + B.n_cls[1] + B.n_cls[2];
+  if (n <= 0) return HNV_OK;
+  auto kern = batched_persistent_kernel<T, GA, VA, GL, VL, W>;
+  int per_sm = 0;
+  HNV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPersistThreads, 0));
+  if (per_sm < 1) per_sm = 1;
+  const int64_t tasks = ((int64_t)B.n_cls[0] + (32 / GA) * kTaskPasses - 1) / ((32 / GA) * kTaskPasses) +
+                        ((int64_t)B.n_cls[1] + B.n_cls[2] + 2 * (32 / GL) * kTaskPasses) /
+                            ((32 / GL) * kTaskPasses);
+  const int64_t wpb = kPersistThreads / 32;
+  const int64_t blocks = std::min<int64_t>((tasks + wpb - 1) / wpb, (int64_t)num_sms() * per_sm);
+  BTRACE("launch persistent GA=%d VA=%d GL=%d VL=%d W=%d items=%d tasks<=%lld blocks=%lld", GA,
+         VA, GL, VL, (int)W, n, (long long)tasks, (long long)blocks);
+  return launch("batched_persistent", kern, (unsigned)blocks, kPersistThreads, 0, s,
+                (const int4*)B.items, (const int32_t*)B.item_g, B.n_cls[0], B.n_cls[1],
+                B.n_cls[2], (const GraphSide*)B.sides, B.n_graphs, dv, keep, scale, counter);
+}
+
+// GL = one lane per row vector (at most 32); GA = GL / 4 (at least 1) with
+// the vectors that makes per lane.
+template <typename T, bool W>
+int launch_persistent_dispatch(const BSide& B, int dv, float keep, float scale, int32_t* counter,
+                               cudaStream_t s) {
+  const int GL = std::min(next_pow2(dv), 32);
+  const int VL = next_pow2((dv + GL - 1) / GL);
+#define HNV_PCASE(ga, va, gl, vl)                                                            \
+  if (GL == gl && VL == vl)                                                                  \
+    return launch_persistent<T, ga, va, gl, vl, W>(B, dv, keep, scale, counter, s);
+  HNV_PCASE(1, 1, 1, 1) HNV_PCASE(1, 2, 2, 1) HNV_PCASE(1, 4, 4, 1) HNV_PCASE(2, 4, 8, 1)
+  HNV_PCASE(4, 4, 16, 1) HNV_PCASE(8, 4, 32, 1) HNV_PCASE(8, 8, 32, 2) HNV_PCASE(16, 8, 32, 4)
+  HNV_PCASE(32, 8, 32, 8)
+#undef HNV_PCASE
+  HNV_FAIL(HNV_ERR_UNSUPPORTED_D, "no persistent variant for %d lanes x %d vectors", GL, VL);
+}
+
 template <typename T>
-int enqueue_half(const hnv_batch* b, const BSide& B, int dv, float omega, cudaStream_t s) {
+int enqueue_finalize(const BSide& B, int dv, float keep, float omega, cudaStream_t s);
+
+template <typename T>
+int enqueue_half(const hnv_batch* b, const BSide& B, int dv, float omega, int32_t* counter,
+                 cudaStream_t s) {
   const float keep = 1.0f - omega;
+  if (b->kernel == HNV_BATCH_KERNEL_PERSISTENT) {
+    if (B.weighted)
+      HNV_CHECK((launch_persistent_dispatch<T, true>(B, dv, keep, omega, counter, s)));
+    else
+      HNV_CHECK((launch_persistent_dispatch<T, false>(B, dv, keep, omega, counter, s)));
+    return enqueue_finalize<T>(B, dv, keep, omega, s);
+  }
   const bool conc = b->aux[0] && b->aux[1] && B.n_cls[1] > 0 && B.n_cls[2] > 0;
   cudaStream_t cs[3] = {s, s, s};
   if (conc) {
@@ -602,17 +756,8 @@ int enqueue_half(const hnv_batch* b, const BSide& B, int dv, float omega, cudaSt
       HNV_CHECK((launch_batched_dispatch<T, false>(G, VPL, B, first, B.n_cls[c], dv, keep, omega, cs[c])));
     first += B.n_cls[c];
   }
-  s = cs[2];   // the reduction follows the chunks' class
-  if (B.n_mid + B.n_huge > 0) {
-    constexpr int N = dev::VecT<T>::N;
-    const int32_t mid_blocks = (B.n_mid + kFinThreads / 32 - 1) / (kFinThreads / 32);
-    const size_t smem = sizeof(float) * (size_t)(kFinThreads / dv) * dv * N;
-    BTRACE("launch finalize mid=%d huge=%d smem=%zu", B.n_mid, B.n_huge, smem);
-    HNV_CHECK(launch("batched_finalize", batched_finalize_kernel<T>,
-                     (unsigned)(mid_blocks + B.n_huge), kFinThreads, smem, s,
-                     (const int4*)B.long_desc, (const int32_t*)B.long_g, B.n_mid, B.n_huge,
-                     mid_blocks, (const GraphSide*)B.sides, B.n_graphs, dv, keep, omega));
-  }
+  // the reduction follows the chunks' class
+  HNV_CHECK(enqueue_finalize<T>(B, dv, keep, omega, cs[2]));
   if (conc) {
     cudaStream_t origin = cs[0];
     for (int i = 0; i < 2; ++i) {
@@ -624,8 +769,44 @@ int enqueue_half(const hnv_batch* b, const BSide& B, int dv, float omega, cudaSt
 }
 
 template <typename T>
+int enqueue_finalize(const BSide& B, int dv, float keep, float omega, cudaStream_t s) {
+  if (B.n_mid + B.n_huge <= 0) return HNV_OK;
+  constexpr int N = dev::VecT<T>::N;
+  const int32_t mid_blocks = (B.n_mid + kFinThreads / 32 - 1) / (kFinThreads / 32);
+  const size_t smem = sizeof(float) * (size_t)(kFinThreads / dv) * dv * N;
+  BTRACE("launch finalize mid=%d huge=%d smem=%zu", B.n_mid, B.n_huge, smem);
+  return launch("batched_finalize", batched_finalize_kernel<T>, (unsigned)(mid_blocks + B.n_huge),
+                kFinThreads, smem, s, (const int4*)B.long_desc, (const int32_t*)B.long_g,
+                B.n_mid, B.n_huge, mid_blocks, (const GraphSide*)B.sides, B.n_graphs, dv, keep,
+                omega);
+}
+
+// Counter slots the persistent launches of one V-cycle use: kCountersPerHalf
+// per half-sweep (2 half-sweeps per sweep of every step). Grows the batch's array if needed;
+// a V-cycle already queued on `user` may still use the old array, so that
+// stream is drained before the array is released.
+int ensure_counters(hnv_batch* b, int64_t n, cudaStream_t s, cudaStream_t user) {
+  if (n <= b->counters_n && b->counters) return HNV_OK;
+  if (b->counters) {
+    HNV_CUDA(cudaStreamSynchronize(user));
+    dev_free(b->counters, s);
+  }
+  b->counters = nullptr;
+  b->counters_n = 0;
+  HNV_CHECK(dev_alloc((void**)&b->counters, sizeof(int32_t) * (size_t)(n > 0 ? n : 1), s));
+  b->counters_n = n > 0 ? n : 1;
+  return HNV_OK;
+}
+
+template <typename T>
 int enqueue_vcycle(const hnv_batch* b, int d, float omega, int sweeps, cudaStream_t s) {
   const int dv = (int)(d * sizeof(T) / 16);
+  int32_t* counter = b->counters;
+  if (b->kernel == HNV_BATCH_KERNEL_PERSISTENT) {
+    const int64_t need = (int64_t)(b->Lmax + 1) * sweeps * 2 * kCountersPerHalf;
+    if (need > b->counters_n) HNV_FAIL(HNV_ERR_STATE, "persistent counters not allocated");
+    if (need > 0) HNV_CUDA(cudaMemsetAsync(counter, 0, sizeof(int32_t) * (size_t)need, s));
+  }
   for (int st = b->Lmax; st >= 0; --st) {
     const BStep& S = b->steps[st];
     BTRACE("enqueue step %d copies %d proj %d", st, S.n_copies, S.n_proj);
@@ -642,8 +823,9 @@ int enqueue_vcycle(const hnv_batch* b, int d, float omega, int sweeps, cudaStrea
                        S.proj_total, dv));
     }
     for (int it = 0; it < sweeps; ++it) {
-      HNV_CHECK(enqueue_half<T>(b, S.side[0], dv, omega, s));
-      HNV_CHECK(enqueue_half<T>(b, S.side[1], dv, omega, s));
+      HNV_CHECK(enqueue_half<T>(b, S.side[0], dv, omega, counter, s));
+      HNV_CHECK(enqueue_half<T>(b, S.side[1], dv, omega, counter + kCountersPerHalf, s));
+      if (b->kernel == HNV_BATCH_KERNEL_PERSISTENT) counter += 2 * kCountersPerHalf;
     }
   }
   return HNV_OK;
@@ -654,29 +836,22 @@ int enqueue(const hnv_batch* b, int dt, int d, float omega, int sweeps, cudaStre
                         : enqueue_vcycle<float>(b, d, omega, sweeps, s);
 }
 
-template <typename T>
-int enqueue_step0_sweep(const hnv_batch* b, int d, float omega, cudaStream_t s) {
-  const int dv = (int)(d * sizeof(T) / 16);
-  HNV_CHECK(enqueue_half<T>(b, b->steps[0].side[0], dv, omega, s));
-  return enqueue_half<T>(b, b->steps[0].side[1], dv, omega, s);
-}
-
-// milliseconds of one level-0 sweep over the batch (median of reps)
-int time_step0(const hnv_batch* b, int dt, int d, float omega, cudaStream_t s, float* ms) {
+// milliseconds of one V-cycle of the batch with one sweep per level (median
+// of the timed repetitions; the first run warms the caches)
+int time_vcycle1(const hnv_batch* b, int dt, int d, float omega, cudaStream_t s, float* ms) {
   cudaEvent_t e0, e1;
   HNV_CUDA(cudaEventCreate(&e0));
   HNV_CUDA(cudaEventCreate(&e1));
   std::vector<float> t;
   int rc = HNV_OK;
-  for (int r = 0; r < 5 && rc == HNV_OK; ++r) {
+  for (int r = 0; r < 4 && rc == HNV_OK; ++r) {
     cudaEventRecord(e0, s);
-    rc = dt == HNV_BF16 ? enqueue_step0_sweep<__nv_bfloat16>(b, d, omega, s)
-                        : enqueue_step0_sweep<float>(b, d, omega, s);
+    rc = enqueue(b, dt, d, omega, 1, s);
     cudaEventRecord(e1, s);
     cudaEventSynchronize(e1);
     float x = 0.f;
     cudaEventElapsedTime(&x, e0, e1);
-    if (r > 0) t.push_back(x);    // the first run warms the caches
+    if (r > 0) t.push_back(x);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -794,8 +969,8 @@ int hnv_batch_autotune(hnv_batch* b, hnv_dtype dt, int d, float omega, hnv_batch
   int rc = HNV_OK;
   const std::vector<int64_t> key = tune_key(b, dt, d);
   PlanShape best_shape = b->shape;
-  std::vector<int> best_lanes(3, 0);
-  float best_ms = -1.f;
+  std::vector<int> best_lanes(4, 0);   // lanes of classes A, B, rest; [3]: kernel
+  float best_ms = -1.f, persistent_ms = -1.f;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
@@ -804,12 +979,14 @@ int hnv_batch_autotune(hnv_batch* b, hnv_dtype dt, int d, float omega, hnv_batch
       best_lanes = it->second.second;
     }
   }
-  const bool cached = best_lanes[0] != 0;
+  const bool cached = best_lanes[0] != 0 || best_lanes[3] == HNV_BATCH_KERNEL_PERSISTENT;
   const size_t rb = (dt == HNV_BF16 ? 2 : 4) * (size_t)d;
   const int dv = (int)(rb / 16);
   uint8_t* zbuf = nullptr;
   if (!cached) {
-    // scratch rows for level 0 of every graph (contents do not affect timing)
+    // scratch rows for level 0 of every graph, also read as the coarsest
+    // rows (no graph's coarsest level has more rows than its level 0;
+    // contents do not affect timing)
     const size_t rows = (size_t)b->v_off.back() + b->e_off.back();
     rc = dev_alloc((void**)&zbuf, rows * rb, s);
     if (rc == HNV_OK) {
@@ -817,13 +994,16 @@ int hnv_batch_autotune(hnv_batch* b, hnv_dtype dt, int d, float omega, hnv_batch
       if (e != cudaSuccess) rc = cuda_status(e, "cudaMemsetAsync");
     }
     const PlanShape shapes[3] = {{4, 16, 64}, {2, 8, 32}, {8, 32, 64}};
+    if (rc == HNV_OK) rc = ensure_counters(b, (int64_t)(b->Lmax + 1) * 2 * kCountersPerHalf, s, s);
     for (int si = 0; si < 3 && rc == HNV_OK; ++si) {
+      // plans and work lists depend on the class boundaries only; the lanes
+      // per row and the kernel only change the launches
       b->shape = shapes[si];
       std::fill(b->lanes, b->lanes + 3, 0);
-      rc = build_plans(b, rb, s, 0);
+      rc = build_plans(b, rb, s);
       if (rc == HNV_OK)
-        rc = build_steps(b, dt, d, zbuf, zbuf, zbuf + (size_t)b->v_off.back() * rb, s, 0);
-      // lanes per row of the two short classes
+        rc = build_steps(b, dt, d, zbuf, zbuf, zbuf + (size_t)b->v_off.back() * rb, s);
+      b->kernel = HNV_BATCH_KERNEL_PER_CLASS;
       const int cand_a[3] = {2, 4, 8}, cand_b[3] = {4, 8, 16};
       for (int ia = 0; ia < 3 && rc == HNV_OK; ++ia)
         for (int ib = 0; ib < 3 && rc == HNV_OK; ++ib) {
@@ -832,13 +1012,24 @@ int hnv_batch_autotune(hnv_batch* b, hnv_dtype dt, int d, float omega, hnv_batch
           b->lanes[2] = 0;
           if (class_lanes(b, 0, dv) != cand_a[ia] || class_lanes(b, 1, dv) != cand_b[ib]) continue;
           float ms = 0.f;
-          rc = time_step0(b, dt, d, omega, s, &ms);
+          rc = time_vcycle1(b, dt, d, omega, s, &ms);
           if (rc == HNV_OK && (best_ms < 0.f || ms < best_ms)) {
             best_ms = ms;
             best_shape = shapes[si];
-            best_lanes = {cand_a[ia], cand_b[ib], 0};
+            best_lanes = {cand_a[ia], cand_b[ib], 0, HNV_BATCH_KERNEL_PER_CLASS};
           }
         }
+      // the persistent kernel (its own lanes; the default class boundaries)
+      if (si == 0 && rc == HNV_OK) {
+        std::fill(b->lanes, b->lanes + 3, 0);
+        b->kernel = HNV_BATCH_KERNEL_PERSISTENT;
+        rc = time_vcycle1(b, dt, d, omega, s, &persistent_ms);
+        if (rc == HNV_OK && (best_ms < 0.f || persistent_ms < best_ms)) {
+          best_ms = persistent_ms;
+          best_shape = shapes[si];
+          best_lanes = {0, 0, 0, HNV_BATCH_KERNEL_PERSISTENT};
+        }
+      }
     }
     if (zbuf) dev_free(zbuf, s);
     if (rc == HNV_OK) {
@@ -849,9 +1040,12 @@ int hnv_batch_autotune(hnv_batch* b, hnv_dtype dt, int d, float omega, hnv_batch
   if (rc == HNV_OK) {
     b->shape = best_shape;
     for (int c = 0; c < 3; ++c) b->lanes[c] = best_lanes[c];
+    b->kernel = best_lanes[3];
     free_steps(b, s);
     b->plans_ready = false;
     if (chosen) {
+      chosen->kernel = best_lanes[3];
+      chosen->persistent_ms = persistent_ms;
       chosen->a_max = best_shape.a_max;
       chosen->b_max = best_shape.b_max;
       chosen->c_max = best_shape.c_max;
@@ -870,6 +1064,7 @@ int hnv_batch_autotune(hnv_batch* b, hnv_dtype dt, int d, float omega, hnv_batch
 int hnv_batch_vcycle(hnv_batch* b, const void* z_coarsest, void* z_v_out, void* z_e_out,
                      hnv_dtype dt, int d, float omega, int sweeps_per_level, int use_cuda_graph,
                      hnv_stream_t stream) {
+  NvtxRange nvtx("hnv batch vcycle");
   clear_error_detail();
   if (!b) HNV_FAIL(HNV_ERR_INVALID_ARG, "batch is NULL");
   if (dt != HNV_F32 && dt != HNV_BF16) HNV_FAIL(HNV_ERR_INVALID_ARG, "unknown dtype");
@@ -905,6 +1100,10 @@ int hnv_batch_vcycle(hnv_batch* b, const void* z_coarsest, void* z_v_out, void* 
       b->built_zv = z_v_out;
       b->built_ze = z_e_out;
     }
+    if (b->kernel == HNV_BATCH_KERNEL_PERSISTENT &&
+        (rc = ensure_counters(b, (int64_t)(b->Lmax + 1) * sweeps_per_level * 2 * kCountersPerHalf,
+                              cs, s)) != HNV_OK)
+      break;
     // the caller's stream must see the set-up work done on the batch stream
     {
       const cudaError_t e = cudaStreamSynchronize(cs);
@@ -918,7 +1117,8 @@ int hnv_batch_vcycle(hnv_batch* b, const void* z_coarsest, void* z_v_out, void* 
       BTRACE("direct enqueue rc=%d", rc);
       break;
     }
-    if (!b->exec || b->exec_omega != omega || b->exec_sweeps != sweeps_per_level) {
+    if (!b->exec || b->exec_omega != omega || b->exec_sweeps != sweeps_per_level ||
+        b->exec_kernel != b->kernel) {
       if (b->exec) {
         cudaGraphExecDestroy(b->exec);
         b->exec = nullptr;
@@ -939,6 +1139,7 @@ int hnv_batch_vcycle(hnv_batch* b, const void* z_coarsest, void* z_v_out, void* 
       if (e != cudaSuccess) { b->exec = nullptr; rc = cuda_status(e, "cudaGraphInstantiate"); break; }
       b->exec_omega = omega;
       b->exec_sweeps = sweeps_per_level;
+      b->exec_kernel = b->kernel;
     }
     BTRACE("graph launch (%lld kernels)", (long long)b->exec_kernels);
     cudaError_t e = cudaGraphLaunch(b->exec, s);
@@ -949,6 +1150,17 @@ int hnv_batch_vcycle(hnv_batch* b, const void* z_coarsest, void* z_v_out, void* 
   return rc;
 }
 
+int hnv_batch_set_kernel(hnv_batch* b, int kernel) {
+  clear_error_detail();
+  if (!b) HNV_FAIL(HNV_ERR_INVALID_ARG, "batch is NULL");
+  if (kernel != HNV_BATCH_KERNEL_PER_CLASS && kernel != HNV_BATCH_KERNEL_PERSISTENT)
+    HNV_FAIL(HNV_ERR_INVALID_ARG, "unknown half-sweep kernel %d", kernel);
+  b->kernel = kernel;   // a captured V-cycle of the other kernel is re-captured on next use
+  return HNV_OK;
+}
+
+int hnv_batch_get_kernel(const hnv_batch* b) { return b ? b->kernel : HNV_ERR_INVALID_ARG; }
+
 void hnv_batch_free(hnv_batch* b) {
   if (!b) return;
   int prev = -1;
@@ -957,6 +1169,7 @@ void hnv_batch_free(hnv_batch* b) {
   if (b->cap_stream) {
     free_steps(b, b->cap_stream);
     free_list(b->plan_owned, b->cap_stream);
+    if (b->counters) dev_free(b->counters, b->cap_stream);
     cudaStreamSynchronize(b->cap_stream);
     cudaStreamDestroy(b->cap_stream);
   }

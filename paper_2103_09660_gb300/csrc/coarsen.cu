@@ -331,6 +331,7 @@ __global__ void survivor_rows(int32_t m, const int32_t* __restrict__ keep,
 
 int coarsen_step(hnv_graph* g, int level, const hnv_coarsen_params* p,
                  const uint64_t* d_explicit, Level* fine, Level* coarse) {
+  NvtxRange nvtx("hnv coarsen level %d", level);
   cudaStream_t s = g->stream;
   const int32_t n = fine->n, m = fine->m;
   const int64_t nnz = fine->nnz;

@@ -115,6 +115,15 @@ bool timing_on();
 int timing_begin(int phase, cudaStream_t s, double alg_bytes);
 void timing_end(int slot, cudaStream_t s);
 
+// An NVTX range (named in profiler timelines) for the scope's lifetime.
+// NVTX is header-only: without a tool attached a range costs a check.
+struct NvtxRange {
+  explicit NvtxRange(const char* fmt, ...);
+  ~NvtxRange();
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 struct PhaseScope {
   int slot;
   cudaStream_t s;
@@ -323,6 +332,9 @@ int vcycle_backward_impl(hnv_graph* g, const float* ckpt, const float* g_v0, con
 
 // tma_refine.cu: TMA-gather half-sweep for d in {32, 64, 128, 256}.
 bool tma_supported(int d);
+// One bounded mbarrier wait that nothing completes; sets ERRBIT_TIMEOUT in
+// *err once it gives up after limit_ns.
+int wait_selftest(int32_t* err, uint64_t limit_ns, cudaStream_t s);
 int tma_half_sweep(const SplitPlan& plan, const int32_t* idx, const float* inc_w,
                    const float* inv_norm, const float* src, int64_t src_rows, const float* self_in,
                    float* out, int64_t self_rows, int d, float omega, float* partials,

@@ -443,6 +443,7 @@ int ensure_scratch(float** p, size_t* have, size_t need, cudaStream_t s) {
 
 int refine_level(hnv_graph* g, int level, void* z_v, void* z_e, int dtype, int d, float omega,
                  int sweeps, int mode, cudaStream_t s) {
+  NvtxRange nvtx("hnv refine level %d (%d sweeps)", level, sweeps);
   Level& lv = g->levels[level];
   const size_t es = elem_size(dtype);
   const SplitPlan* planE = &lv.planE;
@@ -504,6 +505,7 @@ int refine_two_phase_with_partials(const hnv_graph* g, int level, float* z_v, fl
 
 int project_level(const hnv_graph* g, int fine_level, const void* zc_v, const void* zc_e,
                   void* zf_v, void* zf_e, int dtype, int d, cudaStream_t s) {
+  NvtxRange nvtx("hnv project onto level %d", fine_level);
   const Level& f = g->levels[fine_level];
   const Level& c = g->levels[fine_level + 1];
   const size_t es = elem_size(dtype);

@@ -6,9 +6,22 @@
 #include <mutex>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "hnv_internal.cuh"
 
 namespace hnv {
+
+NvtxRange::NvtxRange(const char* fmt, ...) {
+  char name[96];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(name, sizeof(name), fmt, ap);
+  va_end(ap);
+  nvtxRangePushA(name);
+}
+
+NvtxRange::~NvtxRange() { nvtxRangePop(); }
 
 // ---------------------------------------------------------------------------
 // Errors
@@ -72,6 +85,42 @@ static hnv_alloc_fn g_alloc = nullptr;
 static hnv_free_fn g_free = nullptr;
 static void* g_alloc_ctx = nullptr;
 
+// The library's own stream-ordered memory pool per device. Its release
+// threshold is unlimited: memory freed by one call stays mapped for the
+// next (the default pool returns it to the system at every synchronisation,
+// and a V-cycle step allocates and frees about 1.5 GB at the 1M-node size).
+// hnv_release_cached_memory() gives the unused part back.
+constexpr int kMaxPoolDevices = 64;
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pools[kMaxPoolDevices] = {nullptr};
+
+static int device_pool(cudaMemPool_t* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_status(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxPoolDevices) HNV_FAIL(HNV_ERR_INVALID_ARG, "device %d", dev);
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    e = cudaMemPoolCreate(&pool, &props);
+    if (e != cudaSuccess) return cuda_status(e, "cudaMemPoolCreate");
+    uint64_t keep = ~0ull;
+    e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) {
+      cudaMemPoolDestroy(pool);
+      return cuda_status(e, "cudaMemPoolSetAttribute");
+    }
+    g_pools[dev] = pool;
+  }
+  *out = g_pools[dev];
+  return HNV_OK;
+}
+
 int dev_alloc(void** p, size_t bytes, cudaStream_t s) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
@@ -80,12 +129,14 @@ int dev_alloc(void** p, size_t bytes, cudaStream_t s) {
     if (!*p) HNV_FAIL(HNV_ERR_OOM, "allocator hook returned NULL for %zu bytes", bytes);
     return HNV_OK;
   }
-  cudaError_t e = cudaMallocAsync(p, bytes, s);
+  cudaMemPool_t pool = nullptr;
+  HNV_CHECK(device_pool(&pool));
+  cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, s);
   if (e != cudaSuccess) {
     *p = nullptr;
     cudaGetLastError();
     HNV_FAIL(e == cudaErrorMemoryAllocation ? HNV_ERR_OOM : HNV_ERR_CUDA,
-             "cudaMallocAsync(%zu bytes): %s", bytes, cudaGetErrorString(e));
+             "cudaMallocFromPoolAsync(%zu bytes): %s", bytes, cudaGetErrorString(e));
   }
   return HNV_OK;
 }
@@ -171,6 +222,16 @@ int hnv_set_allocator(hnv_alloc_fn alloc_fn, hnv_free_fn free_fn, void* ctx) {
   g_alloc = alloc_fn;
   g_free = free_fn;
   g_alloc_ctx = ctx;
+  return HNV_OK;
+}
+
+int hnv_release_cached_memory(void) {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  for (int d = 0; d < kMaxPoolDevices; ++d) {
+    if (!g_pools[d]) continue;
+    const cudaError_t e = cudaMemPoolTrimTo(g_pools[d], 0);
+    if (e != cudaSuccess) return cuda_status(e, "cudaMemPoolTrimTo");
+  }
   return HNV_OK;
 }
 

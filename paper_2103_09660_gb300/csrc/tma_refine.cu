@@ -421,7 +421,26 @@ int run_tma_classes(const CUtensorMap& msrc, const CUtensorMap& mself, const Spl
                                      out, omega, partials, err, s);
 }
 
+// Self-test of the bounded waits: one warp initialises an mbarrier that
+// nothing arrives at (no copy is issued, nothing is expected) and waits on
+// its first phase with mbar_wait_bounded, the helper the TMA gather uses.
+// The wait must give up after limit_ns; the kernel then records the timeout
+// in the error word exactly as the gather does.
+__global__ void wait_selftest_kernel(uint64_t limit_ns, int32_t* err) {
+  __shared__ __align__(8) uint64_t bar;
+  const uint32_t b = smem_u32(&bar);
+  if (threadIdx.x == 0) mbar_init(b, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  __syncwarp();
+  const bool done = mbar_wait_bounded(b, 0, limit_ns);
+  if (!done && threadIdx.x == 0) atomicOr(err, (int32_t)ERRBIT_TIMEOUT);
+}
+
 }  // namespace
+
+int wait_selftest(int32_t* err, uint64_t limit_ns, cudaStream_t s) {
+  return launch("wait_selftest", wait_selftest_kernel, 1, 32, 0, s, limit_ns, err);
+}
 
 bool tma_supported(int d) { return d == 32 || d == 64 || d == 128 || d == 256; }
 

@@ -56,11 +56,20 @@ def test_batch_equals_per_graph(H, dtname, d):
     depths = {G.num_levels for G in Gs}
     assert len(depths) > 1            # graphs of different depth in one batch
     with H.Batch(Gs) as B:
+        assert B.kernel == H.BATCH_KERNEL_PER_CLASS           # the default
         co, vo, eo = B.offsets()
         zc = torch.randn((int(co[-1]), d), device="cuda").to(dt)
         zv = torch.empty((int(vo[-1]), d), dtype=dt, device="cuda")
         ze = torch.empty((int(eo[-1]), d), dtype=dt, device="cuda")
-        for use_graph in (False, True, True):      # direct, capture, replay
+        # both half-sweep kernels; direct launches, capture, replay, and a
+        # switch back to the first kernel (re-capture)
+        for kernel, use_graph in ((H.BATCH_KERNEL_PERSISTENT, False),
+                                  (H.BATCH_KERNEL_PERSISTENT, True),
+                                  (H.BATCH_KERNEL_PERSISTENT, True),
+                                  (H.BATCH_KERNEL_PER_CLASS, False),
+                                  (H.BATCH_KERNEL_PER_CLASS, True),
+                                  (H.BATCH_KERNEL_PERSISTENT, True)):
+            B.kernel = kernel
             zv.fill_(float("nan"))
             ze.fill_(float("nan"))
             B.vcycle(zc, zv, ze, 0.5, 4, use_cuda_graph=use_graph)
@@ -70,6 +79,8 @@ def test_batch_equals_per_graph(H, dtname, d):
             for i, G in enumerate(Gs):
                 sv, se = _run_single(H, G, zc[co[i]:co[i + 1]].contiguous(), d, dt, 4)
                 assert torch.equal(sv, zv[vo[i]:vo[i + 1]]) and torch.equal(se, ze[eo[i]:eo[i + 1]])
+        with pytest.raises(H.HNVError):
+            B.kernel = 7
     for G in Gs:
         G.close()
 
@@ -87,11 +98,14 @@ def test_batch_autotune_keeps_results_and_matches_oracle(H):
         before = (zv.clone(), ze.clone())
         t = B.autotune(H.F32, d)
         assert t["a_max"] < t["b_max"] < t["c_max"] and t["lanes_a"] >= 1
+        assert t["kernel"] == B.kernel and t["persistent_ms"] > 0 and t["best_ms"] > 0
+        assert t["best_ms"] <= t["persistent_ms"]
         B.vcycle(zc, zv, ze, 0.5, 3)
         torch.cuda.synchronize()
         assert torch.equal(before[0], zv) and torch.equal(before[1], ze)
         t2 = B.autotune(H.F32, d)
         assert t2["from_cache"] == 1 and t2["a_max"] == t["a_max"]
+        assert t2["kernel"] == t["kernel"] == B.kernel
         # two graphs against the FP64 oracle
         for i in (0, len(Gs) - 1):
             lv0 = oracle_level0(hgs[i])
@@ -151,7 +165,11 @@ def test_batch_edge_shapes(H, dtname, d):
         zc = torch.randn((int(co[-1]), d), device="cuda").to(dt)
         zv = torch.empty((int(vo[-1]), d), dtype=dt, device="cuda")
         ze = torch.empty((int(eo[-1]), d), dtype=dt, device="cuda")
-        for omega, sweeps in ((0.5, 3), (0.5, 0), (0.0, 2)):
+        for kernel, omega, sweeps in ((H.BATCH_KERNEL_PERSISTENT, 0.5, 3),
+                                      (H.BATCH_KERNEL_PER_CLASS, 0.5, 3),
+                                      (H.BATCH_KERNEL_PERSISTENT, 0.5, 0),
+                                      (H.BATCH_KERNEL_PERSISTENT, 0.0, 2)):
+            B.kernel = kernel
             B.vcycle(zc, zv, ze, omega, sweeps)
             torch.cuda.synchronize()
             for i, G in enumerate(Gs):
