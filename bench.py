@@ -100,6 +100,26 @@ def shard_units(weights, ws: int, rank: int) -> list:
     return sorted(mine)
 
 
+def _rank_entry(rank, n, port, target, argv):
+    os.environ.update(RANK=str(rank), LOCAL_RANK=str(rank), WORLD_SIZE=str(n),
+                      LOCAL_WORLD_SIZE=str(n), MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    target(argv)
+
+
+def spawn_ranks(n: int, target, argv) -> None:
+    """Runs target(argv) in n child processes with the torch.distributed
+    environment set as torchrun sets it (RANK, LOCAL_RANK, WORLD_SIZE,
+    MASTER_ADDR=127.0.0.1, a free MASTER_PORT): `bench.py --gpus N` started
+    without a launcher starts its own ranks. Raises if a rank fails."""
+    import socket
+    import torch.multiprocessing as mp
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    mp.start_processes(_rank_entry, args=(n, port, target, argv), nprocs=n, join=True,
+                       start_method="spawn")
+
+
 def aggregate(units_per_rank: float, seconds: list) -> float:
     """Whole-job throughput: units of all ranks over the slowest rank."""
     return units_per_rank * len(seconds) / max(seconds)
@@ -170,39 +190,175 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle sample (the cpu_baseline leg and the reference arm)
+# CPU oracle baseline (the cpu_baseline leg, the reference arm, --oracle-study)
+#
+# The FP64 oracle runs the same V-cycle on the host cores. Its coarsening is
+# sequential integer work and is timed once, on one core. Projection and
+# refinement act on every embedding column on its own, so a block of columns
+# is the same computation restricted to those columns: worker processes,
+# forked before this process touches CUDA, take column blocks. Throughput is
+# refinement updates (2 * nnz_l * d * sweeps per level) per second.
 # ---------------------------------------------------------------------------
 
-_SAMPLES = {}
+_OH = {}   # the oracle hierarchy and coarsest rows, set before workers fork
 
 
-def oracle_sample(hg, spec, fraction: float = 1.0):
-    """One two-phase refinement sweep of level 0 by the FP64 oracle on the
-    first `fraction` of the hyperedges (all their members). Returns
-    (updates, seconds, description); the sample level is built once."""
+def host_cores() -> int:
+    return len(os.sched_getaffinity(0))
+
+
+def oracle_prepare(hg, spec):
+    """Builds the oracle's hierarchy (timed: level-0 incidence, coarsening)
+    and the coarsest rows; kept in _OH for forked workers."""
     from oracle import hnv_oracle as O
-    m_s = max(1, int(round(hg.m * fraction)))
-    key = (id(hg), m_s, spec.d)
-    if key not in _SAMPLES:
-        nnz_s = int(hg.edge_ptr[m_s])
-        lv = O.build_level(hg.n, m_s, hg.edge_ptr[:m_s + 1], hg.edge_nodes[:nnz_s],
-                           hg.weights[:m_s])
-        rng = np.random.default_rng(7)
-        _SAMPLES[key] = (lv, rng.standard_normal((lv.n, spec.d)),
-                         rng.standard_normal((lv.m, spec.d)))
-    lv, z_v, z_e = _SAMPLES[key]
     t0 = time.perf_counter()
-    O.refine(lv, z_v, z_e, 0.5, 1, O.SWEEP_TWO_PHASE)
-    dt = time.perf_counter() - t0
-    upd = 2.0 * lv.nnz * spec.d
-    desc = ("one two-phase refinement sweep of level 0 restricted to the first %d of %d "
-            "hyperedges (nnz %d, d %d), FP64 numpy/scipy oracle" % (m_s, hg.m, lv.nnz, spec.d))
-    return upd, dt, desc
+    lv0 = O.build_level(hg.n, hg.m, hg.edge_ptr, hg.edge_nodes, hg.weights)
+    t1 = time.perf_counter()
+    h = O.coarsen(lv0, O.CoarsenParams(min_nodes=spec.min_nodes, max_levels=spec.max_levels,
+                                       seed=spec.seed))
+    t2 = time.perf_counter()
+    top = h.levels[-1]
+    _OH["h"] = h
+    _OH["zc"] = hypergen.coarsest_embedding(top.n + top.m, spec.d, seed=spec.seed).astype(np.float64)
+    _OH["sweeps"] = spec.sweeps
+    return {"build_s": t1 - t0, "coarsen_s": t2 - t1}
 
 
-def oracle_threads() -> int:
-    # scipy's CSR product and numpy elementwise ops run on one thread here
-    return 1
+def _oracle_vcycle_worker(cols):
+    """The oracle V-cycle (refine the coarsest level, then project and refine
+    every finer level) on the given columns; seconds per phase and updates."""
+    from oracle import hnv_oracle as O
+    h, sweeps = _OH["h"], _OH["sweeps"]
+    z = _OH["zc"][:, cols]
+    L = len(h.levels) - 1
+    tr = tp = 0.0
+    upd = 0.0
+    top = h.levels[L]
+    t0 = time.perf_counter()
+    z_v, z_e = O.refine(top, z[:top.n], z[top.n:], 0.5, sweeps)
+    tr += time.perf_counter() - t0
+    upd += 2.0 * top.nnz * len(cols) * sweeps
+    for ell in range(L - 1, -1, -1):
+        t0 = time.perf_counter()
+        z_v, z_e = O.project(h.rep_v[ell], h.rep_e[ell], z_v, z_e)
+        t1 = time.perf_counter()
+        z_v, z_e = O.refine(h.levels[ell], z_v, z_e, 0.5, sweeps)
+        t2 = time.perf_counter()
+        tp += t1 - t0
+        tr += t2 - t1
+        upd += 2.0 * h.levels[ell].nnz * len(cols) * sweeps
+    return {"refine_s": tr, "project_s": tp, "updates": upd}
+
+
+def _oracle_level_worker(args):
+    """One level of the V-cycle (project from seeded coarse rows, then the
+    level's sweeps) on the given columns; the reference arm's step sample."""
+    from oracle import hnv_oracle as O
+    ell, cols = args
+    h, sweeps = _OH["h"], _OH["sweeps"]
+    lv = h.levels[ell]
+    rng = np.random.default_rng(1000 + ell)
+    t0 = time.perf_counter()
+    if ell + 1 < len(h.levels):
+        c = h.levels[ell + 1]
+        zc = rng.standard_normal((c.n + c.m, len(cols)))
+        t0 = time.perf_counter()
+        z_v, z_e = O.project(h.rep_v[ell], h.rep_e[ell], zc[:c.n], zc[c.n:])
+    else:
+        z = _OH["zc"][:, cols]
+        z_v, z_e = z[:lv.n], z[lv.n:]
+    t1 = time.perf_counter()
+    O.refine(lv, z_v, z_e, 0.5, sweeps)
+    t2 = time.perf_counter()
+    return {"refine_s": t2 - t1, "project_s": t1 - t0,
+            "updates": 2.0 * lv.nnz * len(cols) * sweeps}
+
+
+def oracle_pool(procs):
+    """A pool forked now (the caller has not initialised CUDA), sharing _OH."""
+    import multiprocessing as mp
+    return mp.get_context("fork").Pool(procs)
+
+
+def oracle_vcycle_timed(pool, procs, cols_per_proc, d):
+    """The oracle V-cycle on procs * cols_per_proc columns, one block per
+    process (all at once); wall time and summed per-phase worker seconds."""
+    blocks = [list(range(i * cols_per_proc, (i + 1) * cols_per_proc)) for i in range(procs)]
+    blocks = [[c % d for c in b] for b in blocks]
+    t0 = time.perf_counter()
+    parts = pool.map(_oracle_vcycle_worker, blocks) if procs > 1 else [_oracle_vcycle_worker(blocks[0])]
+    wall = time.perf_counter() - t0
+    return {"wall_s": wall, "columns": procs * cols_per_proc,
+            "updates": sum(p["updates"] for p in parts),
+            "refine_s_max": max(p["refine_s"] for p in parts),
+            "project_s_max": max(p["project_s"] for p in parts)}
+
+
+def cpu_baseline_line(hg, spec, prep, pool, procs):
+    """cpu_baseline of the bench line: the oracle V-cycle on all host cores
+    (one column per process) and on one core (one column), scaled to the
+    workload's d columns; coarsening (one core) added once."""
+    d = spec.d
+    allc = oracle_vcycle_timed(pool, procs, 1, d)
+    one = oracle_vcycle_timed(None, 1, 1, d)
+    full_updates = allc["updates"] / allc["columns"] * d
+    # all cores: d columns take ceil(d / procs) rounds of the measured wall time
+    rounds = -(-d // procs)
+    t_all = prep["build_s"] + prep["coarsen_s"] + rounds * allc["wall_s"]
+    t_one = prep["build_s"] + prep["coarsen_s"] + d * one["wall_s"]
+    return {
+        "value": full_updates / t_all, "unit": UNIT, "cores": procs, "kind": "oracle",
+        "sample": ("FP64 oracle V-cycle of the workload (5 levels, %d sweeps per level): "
+                   "incidence build and coarsening timed whole on one core; projection and "
+                   "refinement on %d of the %d columns, one per process on %d cores, scaled "
+                   "to %d columns (%d rounds)" % (spec.sweeps, allc["columns"], d, procs, d,
+                                                   rounds)),
+        "seconds_per_vcycle": t_all,
+        "phases_s": {"build": prep["build_s"], "coarsen": prep["coarsen_s"],
+                     "refine_project_all_cores_per_round": allc["wall_s"],
+                     "refine_per_round": allc["refine_s_max"],
+                     "project_per_round": allc["project_s_max"]},
+        "one_core": {"value": full_updates / t_one, "cores": 1, "seconds_per_vcycle": t_one,
+                     "sample": "the same V-cycle on one column in one process, scaled to %d "
+                               "columns" % d},
+        "host_cores_available": host_cores(),
+    }
+
+
+def run_oracle_study(args):
+    """The FP64 oracle's whole V-cycle per phase on all host cores (column
+    blocks across processes) and on one core, every column, median of 3."""
+    spec = hypergen.CONFIGS[args.workload]
+    hg = hypergen.generate(spec)
+    prep = oracle_prepare(hg, spec)
+    procs = host_cores()
+    d = spec.d
+    pool = oracle_pool(procs)
+    runs_all, runs_one = [], []
+    for _ in range(3):
+        runs_all.append(oracle_vcycle_timed(pool, procs, -(-d // procs), d))
+    pool.close()
+    one_cols = -(-d // procs)
+    for _ in range(3):
+        runs_one.append(oracle_vcycle_timed(None, 1, one_cols, d))
+    med = lambda xs, k: float(np.median([x[k] for x in xs]))
+    updates = runs_all[0]["updates"] / runs_all[0]["columns"] * d
+    t_all = prep["build_s"] + prep["coarsen_s"] + med(runs_all, "wall_s")
+    t_one = prep["build_s"] + prep["coarsen_s"] + med(runs_one, "wall_s") * d / one_cols
+    print(json.dumps({
+        "study": "FP64 oracle V-cycle on the host cores", "workload": args.workload,
+        "n": hg.n, "m": hg.m, "nnz": hg.nnz, "d": d, "sweeps_per_level": spec.sweeps,
+        "levels": len(_OH["h"].levels), "updates_per_vcycle": updates,
+        "build_s": prep["build_s"], "coarsen_s": prep["coarsen_s"],
+        "all_cores": {"cores": procs, "columns_per_process": -(-d // procs),
+                      "refine_project_wall_s_median": med(runs_all, "wall_s"),
+                      "refine_s_median": med(runs_all, "refine_s_max"),
+                      "project_s_median": med(runs_all, "project_s_max"),
+                      "vcycle_s": t_all, "updates_per_s": updates / t_all},
+        "one_core": {"cores": 1, "columns_measured": one_cols,
+                     "refine_project_s_median": med(runs_one, "wall_s"),
+                     "vcycle_s_scaled": t_one, "updates_per_s": updates / t_one},
+        "runs": 3}))
 
 
 # ---------------------------------------------------------------------------
@@ -212,7 +368,7 @@ def oracle_threads() -> int:
 TRAFFIC_SOURCES = ("paper_2103_09660_gb300/csrc/refine.cu",
                    "paper_2103_09660_gb300/csrc/refine_device.cuh",
                    "paper_2103_09660_gb300/csrc/incidence.cu")
-TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "traffic_refine_planted_1m.md")
+TRAFFIC_JSON = os.path.join(ROOT, "profiles", "traffic_refine_planted_1m.json")
 
 
 def source_hash():
@@ -225,26 +381,22 @@ def source_hash():
 
 
 def load_traffic(kernel_tag):
-    """DRAM bytes per half-sweep from the committed ncu summary (its JSON
-    block), if it was taken on the current kernel sources; else None."""
-    if not os.path.exists(TRAFFIC_SUMMARY):
-        return None
+    """DRAM bytes per half-sweep from the committed ncu data file, if it was
+    taken on the current kernel sources; else None."""
     try:
-        text = open(TRAFFIC_SUMMARY).read()
-        block = text.split("```json", 1)[1].split("```", 1)[0]
-        rec = json.loads(block).get(kernel_tag)
-    except (OSError, ValueError, IndexError):
+        rec = json.load(open(TRAFFIC_JSON)).get(kernel_tag)
+    except (OSError, ValueError):
         return None
     if not rec or rec.get("source_sha256_16") != source_hash():
         return None
     return rec.get("dram_bytes_per_launch")
 
 
-def traffic_summary(csv_path):
-    """Reads an ncu CSV of gpu__time_duration.sum, dram__bytes_read.sum and
-    dram__bytes_write.sum over whole V-cycles and prints, per refinement
-    side, the DRAM bytes and time per half-sweep (a half-sweep is the run of
-    that side's gather launches plus its split-row reduction)."""
+def _half_sweeps(csv_path):
+    """Per side, the DRAM bytes and ncu time of each half-sweep in an ncu CSV
+    of gpu__time_duration.sum, dram__bytes_read.sum and dram__bytes_write.sum
+    over refinement launches (a half-sweep: one side's gather launches, then
+    its split-row reduction)."""
     import csv
     rows = list(csv.reader(open(csv_path)))
     hdr = next(i for i, r in enumerate(rows) if "Kernel Name" in r and "Metric Name" in r)
@@ -257,34 +409,50 @@ def traffic_summary(csv_path):
             continue
         rec = launches.setdefault(int(r[ii]), {"name": r[ki]})
         rec[r[mi]] = float(r[vi].replace(",", ""))
-    acc = {"E": [0.0, 0.0, 0], "V": [0.0, 0.0, 0]}
+    out = {"E": [], "V": []}
     phase = None
     for lid in sorted(launches):
         rec = launches[lid]
         name = rec["name"]
         if "gather_packed" in name:             # the packed short rows: hyperedge side
             side = "E"
-            if side != phase:
-                acc[side][2] += 1
-            phase = side
         elif "gather_kernel<" in name and "batched" not in name:
             side = "V" if name.split("<", 1)[1].split(">", 1)[0].rstrip().endswith("1") else "E"
-            if side != phase:
-                acc[side][2] += 1
-            phase = side
         elif "finalize_kernel<" in name and phase is not None and "batched" not in name:
             side = phase
         else:
             phase = None
             continue
-        acc[side][0] += rec.get("dram__bytes_read.sum", 0.0) + rec.get("dram__bytes_write.sum", 0.0)
-        acc[side][1] += rec.get("gpu__time_duration.sum", 0.0)
+        if side != phase and not name.startswith("finalize"):
+            out[side].append([0.0, 0.0])
+        phase = side
+        out[side][-1][0] += rec.get("dram__bytes_read.sum", 0.0) + rec.get("dram__bytes_write.sum", 0.0)
+        out[side][-1][1] += rec.get("gpu__time_duration.sum", 0.0)
+    return out
+
+
+def traffic_summary(csv_paths):
+    """DRAM bytes per refinement half-sweep, averaged over the levels, from
+    one ncu CSV per level (each capturing one sweep of that level: the
+    launches of `bench.py --refine-level L --sweeps 1` whose names match
+    gather or finalize). Prints the JSON that bench.py reads."""
+    if isinstance(csv_paths, str):
+        csv_paths = [csv_paths]
+    per = {"E": [], "V": []}
+    for p in csv_paths:
+        hs = _half_sweeps(p)
+        for side in ("E", "V"):
+            if hs[side]:
+                b = sum(x[0] for x in hs[side]) / len(hs[side])
+                t = sum(x[1] for x in hs[side]) / len(hs[side])
+                per[side].append({"csv": os.path.basename(p), "dram_bytes": round(b),
+                                  "ncu_us": round(t / 1e3, 1)})
     out = {}
     for side, tag in (("E", "refine_e_half_sweep"), ("V", "refine_v_half_sweep")):
-        b, t, n = acc[side]
-        if n:
-            out[tag] = {"dram_bytes_per_launch": round(b / n), "ncu_us_per_launch": round(t / n / 1e3, 1),
-                        "half_sweeps": n, "source_sha256_16": source_hash()}
+        if per[side]:
+            out[tag] = {"dram_bytes_per_launch":
+                        round(sum(x["dram_bytes"] for x in per[side]) / len(per[side])),
+                        "levels": per[side], "source_sha256_16": source_hash()}
     print(json.dumps(out, indent=1))
 
 
@@ -299,18 +467,28 @@ def measured_peaks():
 
 
 def run_ours(args, ws, rank, local):
+    spec = hypergen.CONFIGS[args.workload]
+    hg = hypergen.generate(spec)
+    # the CPU oracle's workers fork before this process initialises CUDA
+    pool = prep = None
+    procs = host_cores()
+    if not args.no_cpu_baseline and ws == 1:
+        prep = oracle_prepare(hg, spec)
+        pool = oracle_pool(procs)
+
     import torch
     import paper_2103_09660_gb300 as H
     from paper_2103_09660_gb300 import build as B
 
+    if torch.cuda.device_count() <= local:
+        raise SystemExit("rank %d needs GPU %d but %d are visible" %
+                         (rank, local, torch.cuda.device_count()))
     if ws > 1:
         init_dist(ws, "nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     B.build()
     H.lib()
-    spec = hypergen.CONFIGS[args.workload]
-    hg = hypergen.generate(spec)
     stream = torch.cuda.current_stream()
 
     d_ptr = torch.from_numpy(hg.edge_ptr).to(dev)
@@ -403,6 +581,23 @@ def run_ours(args, ws, rank, local):
            pin_zc.numel() * pin_zc.element_size())
     d2h = (out_v.numel() + out_e.numel()) * out_v.element_size()
 
+    # the same host<->device copies alone (pinned buffers, one stream): the
+    # part of the end-to-end time that is transfer
+    ptr_t, nodes_t, w_t = (torch.from_numpy(pin_ptr), torch.from_numpy(pin_nodes),
+                           torch.from_numpy(pin_w))
+    dst = [torch.empty_like(x, device=dev) for x in (ptr_t, nodes_t, w_t, pin_zc)]
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for rep in range(2):
+        c0.record(stream)
+        for src_t, dst_t in zip((ptr_t, nodes_t, w_t, pin_zc), dst):
+            dst_t.copy_(src_t, non_blocking=True)
+        out_v.copy_(z_v, non_blocking=True)
+        out_e.copy_(z_e, non_blocking=True)
+        c1.record(stream)
+        torch.cuda.synchronize()
+    copy_ms = c0.elapsed_time(c1)
+    del dst
+
     if rank != 0:
         return None
 
@@ -425,13 +620,11 @@ def run_ours(args, ws, rank, local):
                 "bytes": "compulsory: neighbour table once, own rows read+written, indices, "
                          "pointers, weights, normalisers"}
 
-    # ---- CPU oracle on a bounded sample ----
+    # ---- CPU oracle on the host cores ----
     cpu = None
-    if not args.no_cpu_baseline and ws == 1:
-        upd, dt, desc = oracle_sample(hg, spec, 1.0)
-        cpu = {"value": upd / dt, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
-               "sample": desc, "seconds": round(dt, 2),
-               "host_cores_available": len(os.sched_getaffinity(0))}
+    if pool is not None:
+        cpu = cpu_baseline_line(hg, spec, prep, pool, procs)
+        pool.close()
 
     value = aggregate(updates, [sec_max / args.steps] * ws)
     line = {
@@ -450,7 +643,9 @@ def run_ours(args, ws, rank, local):
         "cpu_baseline": cpu,
         "e2e": {"value": aggregate(updates, [e2e_max] * ws), "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                "ms_per_step": e2e_max * 1e3, "steps": e2e_steps},
+                "ms_per_step": e2e_max * 1e3, "steps": e2e_steps,
+                "copies_alone_ms": round(copy_ms, 3),
+                "copies_alone_GBps": round((h2d + d2h) / (copy_ms / 1e3) / 1e9, 1)},
         "gpu_launches": int(launches),
         "clocks": clock_rec,
     }
@@ -458,32 +653,48 @@ def run_ours(args, ws, rank, local):
 
 
 def run_reference(args, ws, rank, local):
-    """The reference arm: the CPU FP64 oracle on host cores, rank 0 only."""
+    """The reference arm: the CPU FP64 oracle on the host cores, rank 0 only.
+    Step k is one level of the V-cycle (projection from seeded coarse rows,
+    then the level's sweeps), the levels taken in turn from the coarsest, on
+    one column per process over all host cores; the hierarchy is built once
+    before the steps."""
     if rank != 0:
         return None
     spec = hypergen.CONFIGS[args.workload]
     hg = hypergen.generate(spec)
-    # size the per-step sample so warm-up + timed steps stay within ~3 minutes
-    upd1, dt1, _ = oracle_sample(hg, spec, 0.02)
-    per_full = dt1 / 0.02
-    frac = min(1.0, 150.0 / (max(1, args.steps + args.warmup) * per_full))
-    for _ in range(args.warmup):
-        oracle_sample(hg, spec, frac)
+    prep = oracle_prepare(hg, spec)
+    procs = host_cores()
+    pool = oracle_pool(procs)
+    L = len(_OH["h"].levels)
+    order = list(range(L - 1, -1, -1))
+
+    def step(k):
+        ell = order[k % L]
+        t0 = time.perf_counter()
+        parts = pool.map(_oracle_level_worker, [(ell, [c % spec.d]) for c in range(procs)])
+        return sum(p["updates"] for p in parts), time.perf_counter() - t0
+
+    for k in range(args.warmup):
+        step(k)
     tot_u, tot_t = 0.0, 0.0
-    desc = ""
-    for _ in range(args.steps):
-        u, t, desc = oracle_sample(hg, spec, frac)
+    for k in range(args.steps):
+        u, t = step(args.warmup + k)
         tot_u += u
         tot_t += t
+    pool.close()
     value = tot_u / tot_t
+    sample = ("FP64 oracle, one V-cycle level per step (levels in turn from the coarsest: "
+              "projection and %d sweeps) on %d columns, one per process on %d cores; "
+              "hierarchy built once before the steps (build %.1f s, coarsening %.1f s)"
+              % (spec.sweeps, procs, procs, prep["build_s"], prep["coarsen_s"]))
     return {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_t / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": workload_config(args, spec, hg, ws),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
-                         "sample": desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle",
+                         "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -812,19 +1023,41 @@ def run_batch_study(args):
         return {"ms": ms, "updates_per_s": total_updates / (ms / 1e3),
                 "launches_rank0": int(H.kernel_launch_count() - l0)}
 
+    # compulsory bytes of the batched sweeps per V-cycle (the refinement
+    # half-sweeps' formula of the single-graph roofline, summed over graphs
+    # and levels; projection not included)
+    def sweep_bytes(es):
+        tot = 0.0
+        for G in Gs:
+            for lv in range(G.num_levels):
+                n, m, nnz = G.level_info(lv)
+                be = es * (n * d + 2.0 * m * d) + 4.0 * (nnz + 2.0 * m + 1.0)
+                bv = es * (m * d + 2.0 * n * d) + 4.0 * (2.0 * nnz + 2.0 * n + 1.0)
+                tot += k * (be + bv)
+        return tot
+    peak = float(measured_peaks()[0].get("hbm_gbs", 6800.0))
+
     res = {}
     res["loop_f32"] = timed(lambda: loop("f32"))
     res["loop_bf16"] = timed(lambda: loop("bf16"))
-    res["batched_f32_direct"] = timed(batched("f32", False))
-    res["batched_f32_graph"] = timed(batched("f32", True))
-    res["batched_bf16_direct"] = timed(batched("bf16", False))
-    res["batched_bf16_graph"] = timed(batched("bf16", True))
+    for kname, kern in (("per_class", H.BATCH_KERNEL_PER_CLASS),
+                        ("persistent", H.BATCH_KERNEL_PERSISTENT)):
+        bat.kernel = kern
+        res["batched_f32_%s_direct" % kname] = timed(batched("f32", False))
+        res["batched_f32_%s_graph" % kname] = timed(batched("f32", True))
+        res["batched_bf16_%s_direct" % kname] = timed(batched("bf16", False))
+        res["batched_bf16_%s_graph" % kname] = timed(batched("bf16", True))
     t0 = time.time()
     tune = bat.autotune(H.BF16, d, om)
     t_tune = time.time() - t0
     res["batched_bf16_graph_tuned"] = timed(batched("bf16", True))
     tune32 = bat.autotune(H.F32, d, om)
     res["batched_f32_graph_tuned"] = timed(batched("f32", True))
+    for key, r in res.items():
+        if key.startswith("batched"):
+            by = sweep_bytes(2 if "bf16" in key else 4)
+            r["sweep_compulsory_GB"] = by / 1e9
+            r["roofline_frac_of_measured_hbm"] = by / (r["ms"] / 1e3) / 1e9 / peak
     levels = [G.num_levels for G in Gs]
     for G in Gs:
         G.sync_status()
@@ -843,6 +1076,10 @@ def run_batch_study(args):
         "updates_per_vcycle_rank0": updates, "results": res,
         "speedup_batched_bf16_tuned_vs_loop_f32":
             res["loop_f32"]["ms"] / res["batched_bf16_graph_tuned"]["ms"],
+        "speedup_batched_f32_tuned_vs_loop_f32":
+            res["loop_f32"]["ms"] / res["batched_f32_graph_tuned"]["ms"],
+        "roofline_note": "sweep_compulsory_GB over the whole V-cycle time (projection and "
+                         "launch gaps included) against the measured copy bandwidth",
         "tuning_bf16": tune, "tuning_f32": tune32, "autotune_s": t_tune,
         "generate_s": t_gen, "build_coarsen_s": t_build}))
 
@@ -862,8 +1099,8 @@ def main(argv=None):
                     help="embedding storage of the timed V-cycle (sums are float32 either way)")
     ap.add_argument("--precision-study", action="store_true",
                     help="BF16 vs FP32 per level and V-cycle time (use with --workload planted_4m)")
-    ap.add_argument("--traffic-summary", default=None, metavar="NCU_CSV",
-                    help="print DRAM bytes per refinement half-sweep from an ncu CSV")
+    ap.add_argument("--traffic-summary", default=None, nargs="+", metavar="NCU_CSV",
+                    help="print DRAM bytes per refinement half-sweep from ncu CSVs (one per level)")
     ap.add_argument("--feature-study", action="store_true",
                     help="feature (cosine) vs hash coarsening on the workload")
     ap.add_argument("--feature-dim", type=int, default=32)
@@ -871,10 +1108,20 @@ def main(argv=None):
     ap.add_argument("--batch-study", action="store_true",
                     help="batched V-cycle over many hypergraphs vs looping the single-graph path")
     ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--oracle-study", action="store_true",
+                    help="FP64 oracle V-cycle per phase on all host cores and on one core")
     ap.add_argument("--autograd-study", action="store_true",
                     help="forward+backward vs forward time (use with --workload diff_200k)")
     args = ap.parse_args(argv)
+    if args.gpus < 1:
+        raise SystemExit("--gpus must be >= 1")
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # no launcher: start one rank per GPU here (each rank re-enters main)
+        spawn_ranks(args.gpus, main, list(argv) if argv is not None else sys.argv[1:])
+        return
     ws, rank, local = dist_env()
+    if ws != args.gpus:
+        raise SystemExit("--gpus %d but WORLD_SIZE=%d: launch one rank per GPU" % (args.gpus, ws))
     if args.refine_level is not None:
         run_refine_level(args)
         return
@@ -883,6 +1130,9 @@ def main(argv=None):
         return
     if args.autograd_study:
         run_autograd_study(args)
+        return
+    if args.oracle_study:
+        run_oracle_study(args)
         return
     if args.batch_study:
         run_batch_study(args)

@@ -28,27 +28,47 @@ def test_workload_config_is_the_same_for_both_arms():
     assert bench.workload_config(_Args, spec, hg, 4)["parallelism"] == "replicas"
 
 
-def test_traffic_summary_groups_half_sweeps(tmp_path, capsys):
-    """Two sweeps: hyperedge side = packed short rows + long rows + reduction,
-    node side = weighted short + long rows; a coarsening kernel between."""
+def _ncu_csv(path, seq):
     rows = [["ID", "Kernel Name", "Metric Name", "Metric Unit", "Metric Value"]]
-    seq = [("pack_col_row(int)", 0), ("gather_packed_kernel<float, 16, 2>(x)", 1),
-           ("gather_kernel<float, 32, 1, 0>(x)", 1), ("finalize_kernel<float>(x)", 1),
-           ("gather_kernel<float, 16, 2, 1>(x)", 2), ("gather_kernel<float, 32, 1, 1>(x)", 2),
-           ("gather_packed16_kernel<float, 16, 2>(x)", 3), ("gather_kernel<float, 32, 1, 0>(x)", 3),
-           ("gather_kernel<float, 32, 1, 1>(x)", 4), ("rs_scatter(x)", 0)]
-    for i, (name, _) in enumerate(seq):
+    for i, (name, byts) in enumerate(seq):
         rows.append([str(i), name, "gpu__time_duration.sum", "ns", "1000"])
-        rows.append([str(i), name, "dram__bytes_read.sum", "byte", "100"])
+        rows.append([str(i), name, "dram__bytes_read.sum", "byte", str(byts)])
         rows.append([str(i), name, "dram__bytes_write.sum", "byte", "10"])
-    p = tmp_path / "t.csv"
-    with open(p, "w", newline="") as f:
+    with open(path, "w", newline="") as f:
         f.write("==PROF== a banner line\n")
         csv.writer(f).writerows(rows)
-    bench.traffic_summary(str(p))
+
+
+def test_traffic_summary_groups_half_sweeps_per_level(tmp_path, capsys):
+    """Two levels, one sweep each: hyperedge side = packed short rows + long
+    rows + reduction, node side = weighted short + long rows + reduction;
+    the result averages the levels."""
+    lvl0 = [("gather_packed_kernel<float, 16, 2, 1, 4>(x)", 100),
+            ("gather_packed_kernel<float, 16, 2, 2, 4>(x)", 100),
+            ("gather_kernel<float, 32, 1, 0>(x)", 100), ("finalize_kernel<float>(x)", 100),
+            ("gather_kernel<float, 16, 2, 1>(x)", 100), ("gather_kernel<float, 32, 1, 1>(x)", 100),
+            ("finalize_kernel<float>(x)", 100)]
+    lvl1 = [("gather_packed_kernel<float, 16, 2, 1, 4>(x)", 300),
+            ("gather_kernel<float, 32, 1, 0>(x)", 300),
+            ("gather_kernel<float, 32, 1, 1>(x)", 300)]
+    _ncu_csv(tmp_path / "l0.csv", lvl0)
+    _ncu_csv(tmp_path / "l1.csv", lvl1)
+    bench.traffic_summary([str(tmp_path / "l0.csv"), str(tmp_path / "l1.csv")])
     out = json.loads(capsys.readouterr().out)
     e, v = out["refine_e_half_sweep"], out["refine_v_half_sweep"]
-    assert e["half_sweeps"] == 2 and v["half_sweeps"] == 2
-    assert e["dram_bytes_per_launch"] == (3 + 2) * 110 // 2
-    assert v["dram_bytes_per_launch"] == (2 + 1) * 110 // 2
+    assert [x["dram_bytes"] for x in e["levels"]] == [4 * 110, 2 * 310]
+    assert [x["dram_bytes"] for x in v["levels"]] == [3 * 110, 310]
+    assert e["dram_bytes_per_launch"] == (4 * 110 + 2 * 310) // 2
+    assert v["dram_bytes_per_launch"] == (3 * 110 + 310) // 2
     assert e["source_sha256_16"] == bench.source_hash()
+
+
+def test_traffic_is_read_only_for_the_current_sources(tmp_path, monkeypatch):
+    f = tmp_path / "t.json"
+    f.write_text(json.dumps({"refine_e_half_sweep": {"dram_bytes_per_launch": 5,
+                                                     "source_sha256_16": bench.source_hash()},
+                             "refine_v_half_sweep": {"dram_bytes_per_launch": 7,
+                                                     "source_sha256_16": "stale"}}))
+    monkeypatch.setattr(bench, "TRAFFIC_JSON", str(f))
+    assert bench.load_traffic("refine_e_half_sweep") == 5
+    assert bench.load_traffic("refine_v_half_sweep") is None

@@ -65,3 +65,42 @@ def test_shard_units_is_balanced_and_complete():
         assert sorted(i for p in parts for i in p) == list(range(len(w)))
         loads = [sum(w[i] for i in p) for p in parts]
         assert max(loads) - min(loads) <= max(w)
+
+
+def _spawned_payload(argv):
+    """What each rank runs in the spawn test: the environment torchrun would
+    set, a gloo group, and the max-over-ranks timing of bench.py."""
+    sys.path.insert(0, ROOT)
+    import json
+    import bench
+    import torch.distributed as dist
+    ws, rank, local = bench.dist_env()
+    bench.init_dist(ws, "gloo")
+    t = bench.max_over_ranks(0.5 * (rank + 1), ws)
+    json.dump({"ws": ws, "rank": rank, "local": local, "t": t,
+               "addr": os.environ["MASTER_ADDR"], "argv": argv},
+              open(os.path.join(argv[0], "s%d.json" % rank), "w"))
+    dist.destroy_process_group()
+
+
+def test_spawn_ranks_sets_the_launcher_environment(tmp_path):
+    """bench.py --gpus N without torchrun starts N ranks itself through
+    spawn_ranks; each sees RANK / LOCAL_RANK / WORLD_SIZE and 127.0.0.1."""
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    bench.spawn_ranks(3, _spawned_payload, [str(tmp_path)])
+    r = [json.load(open(tmp_path / ("s%d.json" % i))) for i in range(3)]
+    assert [x["rank"] for x in r] == [0, 1, 2] and [x["local"] for x in r] == [0, 1, 2]
+    assert all(x["ws"] == 3 and x["t"] == 1.5 and x["addr"] == "127.0.0.1" for x in r)
+
+
+def test_gpus_flag_must_match_the_launcher(monkeypatch):
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("RANK", "0")
+    with pytest.raises(SystemExit):
+        bench.main(["--gpus", "4", "--workload", "small_2k"])
+    with pytest.raises(SystemExit):
+        bench.main(["--gpus", "0"])
