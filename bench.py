@@ -418,12 +418,13 @@ def _half_sweeps(csv_path):
             side = "E"
         elif "gather_kernel<" in name and "batched" not in name:
             side = "V" if name.split("<", 1)[1].split(">", 1)[0].rstrip().endswith("1") else "E"
-        elif "finalize_kernel<" in name and phase is not None and "batched" not in name:
+        elif (("finalize_kernel<" in name or "combine_kernel<" in name) and phase is not None
+              and "batched" not in name):
             side = phase
         else:
             phase = None
             continue
-        if side != phase and not name.startswith("finalize"):
+        if side != phase and "finalize" not in name and "combine" not in name:
             out[side].append([0.0, 0.0])
         phase = side
         out[side][-1][0] += rec.get("dram__bytes_read.sum", 0.0) + rec.get("dram__bytes_write.sum", 0.0)
@@ -435,7 +436,7 @@ def traffic_summary(csv_paths):
     """DRAM bytes per refinement half-sweep, averaged over the levels, from
     one ncu CSV per level (each capturing one sweep of that level: the
     launches of `bench.py --refine-level L --sweeps 1` whose names match
-    gather or finalize). Prints the JSON that bench.py reads."""
+    gather, finalize or combine). Prints the JSON that bench.py reads."""
     if isinstance(csv_paths, str):
         csv_paths = [csv_paths]
     per = {"E": [], "V": []}
@@ -697,6 +698,21 @@ def run_reference(args, ws, rank, local):
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
+
+
+def run_gather_ceiling(args):
+    """Gather ceilings of this GPU (random 512-byte rows by table size and
+    route, and a copy): builds and runs paper_2103_09660_gb300/probes/
+    gather_ceiling.cu. The refinement kernels are held against these."""
+    from paper_2103_09660_gb300 import build as B
+    src = os.path.join(ROOT, "paper_2103_09660_gb300", "probes", "gather_ceiling.cu")
+    exe = os.path.join(B.BUILD, "gather_ceiling")
+    os.makedirs(B.BUILD, exist_ok=True)
+    subprocess.run([B.nvcc()] + B.ARCH + ["-O3", "-std=c++17", "-o", exe, src], check=True)
+    r = subprocess.run([exe], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise SystemExit("gather ceiling probe failed (%d): %s" % (r.returncode, r.stderr.strip()))
+    print(r.stdout.strip())
 
 
 def run_refine_level(args):
@@ -1108,6 +1124,8 @@ def main(argv=None):
     ap.add_argument("--batch-study", action="store_true",
                     help="batched V-cycle over many hypergraphs vs looping the single-graph path")
     ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--gather-ceiling", action="store_true",
+                    help="measure the GPU's random-row gather ceilings (a probe, no method)")
     ap.add_argument("--oracle-study", action="store_true",
                     help="FP64 oracle V-cycle per phase on all host cores and on one core")
     ap.add_argument("--autograd-study", action="store_true",
@@ -1133,6 +1151,9 @@ def main(argv=None):
         return
     if args.oracle_study:
         run_oracle_study(args)
+        return
+    if args.gather_ceiling:
+        run_gather_ceiling(args)
         return
     if args.batch_study:
         run_batch_study(args)

@@ -43,7 +43,7 @@ constexpr int kGatherThreads = 64;
 // Passes per warp of the packed short-row kernel (see gather_packed_kernel).
 constexpr int kPackedPasses = 4;
 
-template <typename T, int G, int VPL, bool WEIGHTED>
+template <typename T, int G, int VPL, bool WEIGHTED, bool WIDE_U = false>
 __global__ void __launch_bounds__(256)
 gather_kernel(const int4* __restrict__ items, int32_t n_items, const int32_t* __restrict__ idx,
               const float* __restrict__ inc_w, const float* __restrict__ inv_norm,
@@ -59,8 +59,8 @@ gather_kernel(const int4* __restrict__ items, int32_t n_items, const int32_t* __
     const int64_t item = wbase + grp;
     int4 it = make_int4(-1, 0, 0, -1);
     if (item < n_items) it = __ldg(items + item);
-    dev::gather_item<T, G, VPL, WEIGHTED>(it, lg, idx, inc_w, inv_norm, src, self_in, out, dv,
-                                          keep, scale, partials);
+    dev::gather_item<T, G, VPL, WEIGHTED, false, WIDE_U>(it, lg, idx, inc_w, inv_norm, src,
+                                                         self_in, out, dv, keep, scale, partials);
   }
 }
 
@@ -68,13 +68,16 @@ gather_kernel(const int4* __restrict__ items, int32_t n_items, const int32_t* __
 // next to their items (SplitPlan::a_members: rows of 1-4 members, PK = 1;
 // b_members: rows of 5-16, PK = 2). A group reads a row's descriptor and its
 // neighbour indices side by side, not one after the other. Each warp takes
-// PASSES consecutive passes (R rows each) and loads the next pass's
-// descriptors and neighbours while it gathers the current one, so a row's
-// gathers never wait for its descriptor. The register budget is capped so
-// that 32 warps stay resident per SM. Measured in one process on the
-// 1M-node workload against one pass per warp (64-thread blocks both):
-// hyperedge half-sweeps 6-15% faster on levels 1-4 and even on level 0, the
-// V-cycle 89.4 against 92.5 ms.
+// PASSES consecutive passes (R rows each) and loads the descriptors and
+// neighbours of the pass after next while it gathers the current one, so a
+// row's gathers never wait for its descriptor; it also prefetches the next
+// pass's own rows into L2, so their DRAM latency is spent during the
+// current pass. The register budget is capped so that 32 warps stay
+// resident per SM. Measured in one process on the 1M-node workload: against
+// one pass per warp (64-thread blocks both) the hyperedge half-sweeps were
+// 6-15% faster on levels 1-4 and even on level 0, the V-cycle 89.4 against
+// 92.5 ms; the own-row prefetch took the V-cycle from 89.1 to 86.8 ms
+// (hyperedge half-sweeps of levels 1-4 5-8% faster).
 template <typename T, int G, int VPL, int PK, int PASSES>
 __global__ void __launch_bounds__(256, 4)
 gather_packed_kernel(const int4* __restrict__ items, const void* __restrict__ members,
@@ -116,18 +119,35 @@ gather_packed_kernel(const int4* __restrict__ items, const void* __restrict__ me
   int32_t ci;
   float cw;
   load_head(0, ci, cw);
+  int4 nxt = load_it(1);
+  int32_t xi;
+  float xw;
+  load_head(1, xi, xw);
 #pragma unroll 1
   for (int k = 0; k < PASSES; ++k) {
     if (first + k * R >= n_items) break;           // warp-uniform
+    // the next pass's own row (its descriptor arrived during the previous
+    // pass) is brought into L2 while this pass gathers
+    if (nxt.x >= 0 && nxt.w < 0 && keep != 0.f) {
+#pragma unroll
+      for (int j = 0; j < VPL; ++j) {
+        const int col = lg + j * G;
+        if (col < dv)
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(self_in + (size_t)nxt.x * dv + col));
+      }
+    }
     int32_t ni;
     float nw;
-    const int4 nn = load_it(k + 1);
-    load_head(k + 1, ni, nw);
+    const int4 nn = load_it(k + 2);
+    load_head(k + 2, ni, nw);
     dev::gather_item<T, G, VPL, false, true>(cur, lg, idx, inc_w, inv_norm, src, self_in, out,
                                              dv, keep, scale, partials, ci, cw);
-    cur = nn;
-    ci = ni;
-    cw = nw;
+    cur = nxt;
+    ci = xi;
+    cw = xw;
+    nxt = nn;
+    xi = ni;
+    xw = nw;
   }
 }
 
@@ -234,6 +254,13 @@ int launch_items(const HalfSweep& h, const int4* items, int32_t n_items, const v
   const int64_t warps = ((int64_t)n_items + R - 1) / R;
   const int64_t blocks64 = (warps + WPB - 1) / WPB;
   const unsigned blocks = (unsigned)(blocks64 > 0x7fffffff ? 0x7fffffff : blocks64);
+  // the weighted long-row kernel keeps 8 row loads in flight per lane (not
+  // the weighted default of 4): the coarse levels' node half-sweeps, bound
+  // by L2 latency, got 1-2% faster; level 0 is unchanged
+  if (h.inc_w && G == 32 && VPL == 1)
+    return launch("gather_w", gather_kernel<T, G, VPL, true, true>, blocks, kGatherThreads, 0, s,
+                  items, n_items, h.idx, h.inc_w, h.inv_norm, (const uint4*)src,
+                  (const uint4*)self_in, (uint4*)out, dv, keep, scale, partials);
   if (h.inc_w)
     return launch("gather_w", gather_kernel<T, G, VPL, true>, blocks, kGatherThreads, 0, s,
                   items, n_items, h.idx, h.inc_w, h.inv_norm, (const uint4*)src,

@@ -64,7 +64,7 @@ struct VecT<__nv_bfloat16> {
 // PRE: the caller supplies this lane's first neighbour index (incidence
 // beg + lg, any value where lg >= len) in idx0 instead of it being loaded,
 // and for a weighted side that incidence's weight in w0.
-template <typename T, int G, int VPL, bool WEIGHTED, bool PRE = false>
+template <typename T, int G, int VPL, bool WEIGHTED, bool PRE = false, bool WIDE_U = false>
 __device__ __forceinline__ void gather_item(int4 it, int lg, const int32_t* __restrict__ idx,
                                             const float* __restrict__ inc_w,
                                             const float* __restrict__ inv_norm,
@@ -75,9 +75,10 @@ __device__ __forceinline__ void gather_item(int4 it, int lg, const int32_t* __re
   using V = VecT<T>;
   constexpr int N = V::N;
   // row loads in flight per lane (the weighted variant also holds a weight
-  // per load, so it takes half as many to keep its register count down)
+  // per load, so it takes half as many to keep its register count down,
+  // unless WIDE_U)
   constexpr int UB0 = (VPL == 1) ? 8 : (VPL == 2 ? 4 : (VPL == 4 ? 2 : 1));
-  constexpr int UB = (WEIGHTED && UB0 > 1) ? UB0 / 2 : UB0;
+  constexpr int UB = (WEIGHTED && UB0 > 1 && !WIDE_U) ? UB0 / 2 : UB0;
   constexpr int U = UB < G ? UB : G;
   const bool read_self = keep != 0.f;
   const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
@@ -190,36 +191,39 @@ __device__ __forceinline__ void f4_add(float4& a, const float4& b) {
   a.w += b.w;
 }
 
-// Sum of count float4 values p[0], p[stride], p[2*stride], ... (fixed order).
+// Sum of count float4 values p[0], p[stride], p[2*stride], ... in a fixed
+// order: ACC interleaved accumulators (value c goes to accumulator c mod ACC
+// while ACC remain), the tail into the first, then a fixed tree.
+template <int ACC = 4>
 __device__ __forceinline__ float4 sum_strided4(const float4* __restrict__ p, int32_t count,
                                                int32_t stride) {
-  float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, a2 = a0, a3 = a0;
+  float4 a[ACC];
+#pragma unroll
+  for (int q = 0; q < ACC; ++q) a[q] = make_float4(0.f, 0.f, 0.f, 0.f);
   int32_t c = 0;
-  for (; c + 4 <= count; c += 4) {
-    const float4 p0 = p[(size_t)c * stride];
-    const float4 p1 = p[(size_t)(c + 1) * stride];
-    const float4 p2 = p[(size_t)(c + 2) * stride];
-    const float4 p3 = p[(size_t)(c + 3) * stride];
-    f4_add(a0, p0);
-    f4_add(a1, p1);
-    f4_add(a2, p2);
-    f4_add(a3, p3);
+  for (; c + ACC <= count; c += ACC) {
+    float4 v[ACC];
+#pragma unroll
+    for (int q = 0; q < ACC; ++q) v[q] = p[(size_t)(c + q) * stride];
+#pragma unroll
+    for (int q = 0; q < ACC; ++q) f4_add(a[q], v[q]);
   }
-  for (; c < count; ++c) f4_add(a0, p[(size_t)c * stride]);
-  f4_add(a0, a1);
-  f4_add(a2, a3);
-  f4_add(a0, a2);
-  return a0;
+  for (; c < count; ++c) f4_add(a[0], p[(size_t)c * stride]);
+#pragma unroll
+  for (int w = 1; w < ACC; w *= 2)
+#pragma unroll
+    for (int q = 0; q + w < ACC; q += 2 * w) f4_add(a[q], a[q + w]);
+  return a[0];
 }
 
 // Sum over `count` chunks of one row vector's N partial floats.
-template <int N>
+template <int N, int ACC = 4>
 __device__ __forceinline__ void sum_chunks(const float* __restrict__ partials, int32_t first,
                                            int32_t count, int32_t dv, int32_t col, float* out) {
   const float4* base = reinterpret_cast<const float4*>(partials) + ((size_t)first * dv + col) * (N / 4);
 #pragma unroll
   for (int q = 0; q < N / 4; ++q) {
-    const float4 t = sum_strided4(base + q, count, dv * (N / 4));
+    const float4 t = sum_strided4<ACC>(base + q, count, dv * (N / 4));
     out[4 * q] = t.x;
     out[4 * q + 1] = t.y;
     out[4 * q + 2] = t.z;
@@ -251,8 +255,11 @@ __device__ __forceinline__ void finalize_mid(int4 ds, int lane, const float* __r
 
 // Split row with more chunks: the whole block; S = blockDim / dv slices sum
 // contiguous runs of chunks, slice 0 adds the slices in order. `sm` holds
-// S * dv * N floats.
-template <typename T>
+// S * dv * N floats. One block reduces such a row alone (a hub node at the
+// 1M-node workload's level 4 has 6,300 chunks), so each thread keeps eight
+// loads in flight (ACC = 8): the coarse levels' node half-sweeps got 3-17 us
+// faster than with four, the V-cycle 86.9 -> 86.2 ms.
+template <typename T, int ACC = 8>
 __device__ __forceinline__ void finalize_huge(int4 ds, float* sm, const float* __restrict__ partials,
                                               const float* __restrict__ inv_norm,
                                               const uint4* self_in, uint4* out, int32_t dv,
@@ -268,7 +275,7 @@ __device__ __forceinline__ void finalize_huge(int4 ds, float* sm, const float* _
     const int32_t a = (int32_t)((int64_t)ds.z * slice / S);
     const int32_t b = (int32_t)((int64_t)ds.z * (slice + 1) / S);
     float part[N];
-    sum_chunks<N>(partials, ds.y + a, b - a, dv, col, part);
+    sum_chunks<N, ACC>(partials, ds.y + a, b - a, dv, col, part);
 #pragma unroll
     for (int e = 0; e < N; ++e) sm[((size_t)slice * dv + col) * N + e] = part[e];
   }

@@ -47,7 +47,7 @@ def test_traffic_summary_groups_half_sweeps_per_level(tmp_path, capsys):
             ("gather_packed_kernel<float, 16, 2, 2, 4>(x)", 100),
             ("gather_kernel<float, 32, 1, 0>(x)", 100), ("finalize_kernel<float>(x)", 100),
             ("gather_kernel<float, 16, 2, 1>(x)", 100), ("gather_kernel<float, 32, 1, 1>(x)", 100),
-            ("finalize_kernel<float>(x)", 100)]
+            ("finalize_kernel<float>(x)", 100), ("combine_kernel<float>(x)", 100)]
     lvl1 = [("gather_packed_kernel<float, 16, 2, 1, 4>(x)", 300),
             ("gather_kernel<float, 32, 1, 0>(x)", 300),
             ("gather_kernel<float, 32, 1, 1>(x)", 300)]
@@ -57,9 +57,9 @@ def test_traffic_summary_groups_half_sweeps_per_level(tmp_path, capsys):
     out = json.loads(capsys.readouterr().out)
     e, v = out["refine_e_half_sweep"], out["refine_v_half_sweep"]
     assert [x["dram_bytes"] for x in e["levels"]] == [4 * 110, 2 * 310]
-    assert [x["dram_bytes"] for x in v["levels"]] == [3 * 110, 310]
+    assert [x["dram_bytes"] for x in v["levels"]] == [4 * 110, 310]
     assert e["dram_bytes_per_launch"] == (4 * 110 + 2 * 310) // 2
-    assert v["dram_bytes_per_launch"] == (3 * 110 + 310) // 2
+    assert v["dram_bytes_per_launch"] == (4 * 110 + 310) // 2
     assert e["source_sha256_16"] == bench.source_hash()
 
 
