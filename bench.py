@@ -894,13 +894,53 @@ def run_autograd_study(args):
 
         t_fwd = timed(fwd, args.steps)
         t_fb = timed(fwd_bwd, args.steps)
+        # the backward alone, and its phases (CUDA events the library records
+        # on the launching stream, with each phase's algorithmic bytes)
+        n0, m0 = hg.n, hg.m
+        ck = torch.empty(H.hnv_checkpoint_floats(G.handle, d), device=dev)
+        gen2 = torch.Generator().manual_seed(spec.seed + 1)
+        g_v = torch.randn(n0, d, generator=gen2).to(dev)
+        g_e = torch.randn(m0, d, generator=gen2).to(dev)
+        g_w, g_z = torch.empty(m0, device=dev), torch.empty_like(zc)
+        H.hnv_vcycle_save(G.handle, zc, zv, ze, ck, om, k, G.stream)
+
+        def bwd():
+            H.hnv_vcycle_backward(G.handle, ck, g_v, g_e, g_w, g_z, om, k, G.stream)
+
+        t_bwd = timed(bwd, args.steps)
+        H.timing_reset()
+        H.timing_enable(True)
+        for _ in range(args.steps):
+            bwd()
+        torch.cuda.synchronize()
+        H.timing_enable(False)
+        peak, peak_src = measured_peaks()
+        hbm = float(peak.get("hbm_gbs", 6800.0))
+        phases = {}
+        for nm, ph in (("replay", H.PHASE_ADJOINT_REPLAY), ("reverse", H.PHASE_ADJOINT_REVERSE),
+                       ("project", H.PHASE_ADJOINT_PROJECT)):
+            ms, c, by = H.timing_read(ph)
+            ms, by = ms / args.steps, by / args.steps
+            gbs = by / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+            phases[nm] = {"ms": ms, "alg_GB": by / 1e9, "alg_GBps": gbs,
+                          "frac_of_hbm": gbs / hbm}
+        H.timing_reset()
+        if args.profile_backward:
+            # one backward call bracketed for `ncu --profile-from-start off`
+            torch.cuda.synchronize()
+            torch.cuda.profiler.start()
+            bwd()
+            torch.cuda.synchronize()
+            torch.cuda.profiler.stop()
         G.sync_status()
     print(json.dumps({
         "study": "forward+backward vs forward (float32)", "workload": args.workload,
         "n": hg.n, "m": hg.m, "nnz": hg.nnz, "d": d, "levels": L, "sweeps_per_level": k,
         "loss": "softmax cross-entropy of a seeded %dx%d linear head on a seeded %d-node subset"
                 % (d, classes, len(sub)),
-        "forward_ms": t_fwd, "forward_backward_ms": t_fb, "ratio": t_fb / t_fwd}))
+        "forward_ms": t_fwd, "forward_backward_ms": t_fb, "ratio": t_fb / t_fwd,
+        "backward_ms": t_bwd, "backward_phases": phases,
+        "hbm_peak_GBps": hbm, "peak_source": peak_src + " hbm_gbs (copy bandwidth)"}))
 
 
 def run_feature_study(args):
@@ -1130,6 +1170,9 @@ def main(argv=None):
                     help="FP64 oracle V-cycle per phase on all host cores and on one core")
     ap.add_argument("--autograd-study", action="store_true",
                     help="forward+backward vs forward time (use with --workload diff_200k)")
+    ap.add_argument("--profile-backward", action="store_true",
+                    help="with --autograd-study: one more backward call between "
+                         "cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     args = ap.parse_args(argv)
     if args.gpus < 1:
         raise SystemExit("--gpus must be >= 1")

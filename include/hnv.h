@@ -325,8 +325,11 @@ int hnv_vcycle_save(hnv_graph* g, const float* z_coarsest, float* z_v_out, float
  *                   G_E += omega w_e A_e, G_V *= 1 - omega;
  *   hyperedge half: G_V += omega sum_{e ∋ v} G_E[e]/|e|, G_E *= 1 - omega;
  * projection reverses to a segmented sum over each coarse row's copies. The
- * weights, omega, d and sweeps must be those of the forward call. All device
- * buffers; asynchronous on the stream; deterministic. */
+ * replay keeps z~_v = s_v/D_v of every sweep as the gather computes it, so no
+ * step divides by omega. Working memory, from the library's pool: sweeps x
+ * max_l (n_l + m_l) x d floats of replayed iterates, plus
+ * 2 max_l (n_l + m_l) + 2 max_l n_l + max_l m_l rows of d floats. The weights, omega, d and sweeps must be those of the forward
+ * call. All device buffers; asynchronous on the stream; deterministic. */
 int hnv_vcycle_backward(hnv_graph* g, const float* checkpoints, const float* g_v0,
                         const float* g_e0, float* grad_w0, float* grad_z_coarsest, int d,
                         float omega, int sweeps_per_level, hnv_stream_t stream);
@@ -473,7 +476,11 @@ typedef enum {
   HNV_PHASE_PROJECT = 2,
   HNV_PHASE_REFINE_E = 3,   /* hyperedge half-sweeps (gather node rows)   */
   HNV_PHASE_REFINE_V = 4,   /* node half-sweeps (gather hyperedge rows)   */
-  HNV_PHASE_COUNT = 5
+  /* hnv_vcycle_backward, per level: */
+  HNV_PHASE_ADJOINT_REPLAY = 5,   /* the level's sweeps recomputed           */
+  HNV_PHASE_ADJOINT_REVERSE = 6,  /* the sweeps reversed                     */
+  HNV_PHASE_ADJOINT_PROJECT = 7,  /* weight gradients out, projection reversed */
+  HNV_PHASE_COUNT = 8
 } hnv_phase;
 int hnv_timing_enable(int enable);
 /* Clears the recorded events. */

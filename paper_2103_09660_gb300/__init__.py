@@ -28,6 +28,7 @@ __all__ = [
     "ARR_E_PTR", "ARR_E_NODES", "ARR_V_PTR", "ARR_V_EDGES", "ARR_W", "ARR_REP_V",
     "ARR_REP_E", "ARR_DEG_V",
     "PHASE_BUILD", "PHASE_COARSEN", "PHASE_PROJECT", "PHASE_REFINE_E", "PHASE_REFINE_V",
+    "PHASE_ADJOINT_REPLAY", "PHASE_ADJOINT_REVERSE", "PHASE_ADJOINT_PROJECT",
     "Graph", "hnv_build_incidence", "hnv_coarsen", "hnv_project", "hnv_refine",
     "hnv_vcycle", "hnv_refine_noalloc", "hnv_set_weights", "hnv_checkpoint_floats",
     "hnv_vcycle_save", "hnv_vcycle_backward", "vcycle_autograd", "Batch", "kernel_launch_count",
@@ -44,7 +45,8 @@ F32, BF16 = 0, 1
 BATCH_KERNEL_PER_CLASS, BATCH_KERNEL_PERSISTENT = 0, 1
 (ARR_E_PTR, ARR_E_NODES, ARR_V_PTR, ARR_V_EDGES, ARR_W, ARR_REP_V, ARR_REP_E,
  ARR_DEG_V) = range(8)
-PHASE_BUILD, PHASE_COARSEN, PHASE_PROJECT, PHASE_REFINE_E, PHASE_REFINE_V = range(5)
+(PHASE_BUILD, PHASE_COARSEN, PHASE_PROJECT, PHASE_REFINE_E, PHASE_REFINE_V,
+ PHASE_ADJOINT_REPLAY, PHASE_ADJOINT_REVERSE, PHASE_ADJOINT_PROJECT) = range(8)
 
 ERR_NAMES = {0: "HNV_OK", -1: "HNV_ERR_INVALID_ARG", -2: "HNV_ERR_OUT_OF_RANGE",
              -3: "HNV_ERR_TOO_LARGE", -4: "HNV_ERR_OOM", -5: "HNV_ERR_CUDA",

@@ -233,10 +233,10 @@ struct Level {
   SplitPlan planE, planV;
   // adjoint (built on first use; freed with the level)
   bool adj_ready = false;
-  float* e_invdeg_w = nullptr;   // [nnz] CSR order: 1/deg_v of each member
   float* v_invsize_w = nullptr;  // [nnz] CSC order: 1/|e| of each hyperedge
   int32_t* ch_ptr = nullptr;     // [n_{l+1}+1] children of each coarse node:
   int32_t* ch_idx = nullptr;     //   fine nodes v, then collapsed hyperedges n + e
+  int64_t ch_total = 0;          // entries of ch_idx
   SplitPlan planC;
   std::vector<void*> owned;      // every device allocation of this level
   // panel plans of the two sides (0 hyperedge rows, 1 node rows) for the
@@ -342,10 +342,12 @@ int tma_half_sweep(const SplitPlan& plan, const int32_t* idx, const float* inc_w
 
 // General float32 row gather over a plan (used by the adjoint):
 // out[r] = keep * self[r] + scale * norm[r] * sum_k wgt[k] * src[idx[k]];
-// norm / wgt may be null (1); with keep == 0 self is not read.
+// norm / wgt may be null (1); with keep == 0 self is not read. With conc, a
+// graph with side streams, the plan's row classes run concurrently on them.
 int gather_rows_f32(const SplitPlan& plan, const int32_t* idx, const float* wgt,
                     const float* norm, const float* src, const float* self_in, float* out, int d,
-                    float keep, float scale, float* partials, cudaStream_t s);
+                    float keep, float scale, float* partials, cudaStream_t s,
+                    const hnv_graph* conc = nullptr);
 
 // Two-phase sweeps whose split-row partial sums go to caller-provided
 // scratch (at least max(planE.n_chunks, planV.n_chunks) * d floats); no

@@ -444,11 +444,14 @@ size_t elem_size(int dtype) { return dtype == HNV_BF16 ? 2 : 4; }
 
 // out[row] = keep * self[row] + scale * norm[row] * sum over the plan's row of
 // wgt[k] * src[idx[k]] (float32 rows; see gather_kernel). norm and wgt may be
-// null (1). The load path only.
+// null (1). The load path only; with conc (a graph that has side streams) the
+// row classes run concurrently, as in a refinement half-sweep.
 int gather_rows_f32(const SplitPlan& plan, const int32_t* idx, const float* wgt,
                     const float* norm, const float* src, const float* self_in, float* out, int d,
-                    float keep, float scale, float* partials, cudaStream_t s) {
+                    float keep, float scale, float* partials, cudaStream_t s,
+                    const hnv_graph* conc) {
   HalfSweep h{idx, wgt, norm, &plan, 0, 0, nullptr, false};
+  if (conc && conc->aux[0] && conc->aux[1]) h.conc = conc;
   return run_half<float>(h, src, self_in, out, d, keep, scale, partials, s);
 }
 

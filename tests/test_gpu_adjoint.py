@@ -69,8 +69,14 @@ def _check_case(H, hg, seed, d=8, om=0.5, k=3, min_nodes=2):
     # sums a weight-gradient entry is the difference of (about |G| |z|): an
     # exactly-zero gradient (every member of a hyperedge in one coarse row)
     # is a difference of equal float32 sums and leaves ~eps |G| |z| of noise
+    # (a weight gradient is omega times such a difference, so its floor
+    # scales with omega; at omega = 0 it must be exactly zero)
     floor = 1e-2 * np.abs(gv).max() * np.abs(zc).max()
-    ew = np.abs(dw - dw_ref).max() / max(np.abs(dw_ref).max(), floor)
+    if om == 0.0:
+        assert not np.any(dw)
+        ew = 0.0
+    else:
+        ew = np.abs(dw - dw_ref).max() / max(np.abs(dw_ref).max(), om * floor)
     ez = np.abs(dz - dz_ref).max() / max(np.abs(dz_ref).max(), floor)
     assert ew < GRAD_TOL and ez < GRAD_TOL, (ew, ez, np.abs(dw_ref).max(), np.abs(dw).max())
     return ew, ez
@@ -80,6 +86,16 @@ def test_adjoint_small_random_graphs(H):
     for i, hg in enumerate(small_cases(40, 15, n_max=30, m_max=20)):
         for om in (0.5, 0.3):
             _check_case(H, hg, seed=i, d=4 * (1 + i % 3), om=om, k=2 + i % 3)
+
+
+def test_adjoint_omega_extremes(H):
+    """omega near 0, where z~_v = s_v / D_v carries a weight gradient of
+    size omega and must not be recovered from consecutive iterates (which
+    would leave eps |z| / omega of error in it); omega = 1 (z_v^i = z~_v);
+    omega = 0 (every sweep the identity, weight gradients exactly zero)."""
+    for i, hg in enumerate(small_cases(12, 15, n_max=30, m_max=20)):
+        for om in (0.02, 0.001, 1.0, 0.0):
+            _check_case(H, hg, seed=100 + i, d=8, om=om, k=3)
 
 
 def test_adjoint_skewed_split_rows(H):
@@ -182,3 +198,31 @@ def test_set_weights_rejects_bad_weights(H):
         with pytest.raises(H.HNVError) as ei:
             G.set_weights(w)
         assert ei.value.code == -1
+
+
+def test_backward_phase_timing(H):
+    """The backward records its three phases (replay, reverse, projection)
+    with events and algorithmic bytes when timing is on."""
+    import torch
+    spec = hypergen.CONFIGS["small_2k"]
+    hg = hypergen.generate(spec)
+    rng = np.random.default_rng(3)
+    d, om, k = 16, 0.5, 3
+    with H.Graph.from_hypergraph(hg) as G:
+        L = G.coarsen(min_nodes=spec.min_nodes, seed=0)
+        nL, mL, _ = G.level_info(L - 1)
+        zc = rng.standard_normal((nL + mL, d))
+        gv = rng.standard_normal((hg.n, d))
+        ge = rng.standard_normal((hg.m, d))
+        w0 = rng.uniform(0.5, 2.0, hg.m)
+        H.timing_reset()
+        H.timing_enable(True)
+        try:
+            _gpu_grads(H, G, w0, zc, gv, ge, om, k)
+            torch.cuda.synchronize()
+        finally:
+            H.timing_enable(False)
+        for ph in (H.PHASE_ADJOINT_REPLAY, H.PHASE_ADJOINT_REVERSE, H.PHASE_ADJOINT_PROJECT):
+            ms, launches, by = H.timing_read(ph)
+            assert launches == L and ms > 0 and by > 0, (ph, ms, launches, by)
+        H.timing_reset()
