@@ -302,22 +302,22 @@ def cpu_baseline_line(hg, spec, prep, pool, procs):
     allc = oracle_vcycle_timed(pool, procs, 1, d)
     one = oracle_vcycle_timed(None, 1, 1, d)
     full_updates = allc["updates"] / allc["columns"] * d
-    # all cores: d columns take ceil(d / procs) rounds of the measured wall time
-    rounds = -(-d // procs)
-    t_all = prep["build_s"] + prep["coarsen_s"] + rounds * allc["wall_s"]
+    # all cores: d columns take ceil(d / procs) waves of the measured wall time
+    waves = -(-d // procs)
+    t_all = prep["build_s"] + prep["coarsen_s"] + waves * allc["wall_s"]
     t_one = prep["build_s"] + prep["coarsen_s"] + d * one["wall_s"]
     return {
         "value": full_updates / t_all, "unit": UNIT, "cores": procs, "kind": "oracle",
         "sample": ("FP64 oracle V-cycle of the workload (5 levels, %d sweeps per level): "
                    "incidence build and coarsening timed whole on one core; projection and "
                    "refinement on %d of the %d columns, one per process on %d cores, scaled "
-                   "to %d columns (%d rounds)" % (spec.sweeps, allc["columns"], d, procs, d,
-                                                   rounds)),
+                   "to %d columns (%d waves)" % (spec.sweeps, allc["columns"], d, procs, d,
+                                                   waves)),
         "seconds_per_vcycle": t_all,
         "phases_s": {"build": prep["build_s"], "coarsen": prep["coarsen_s"],
-                     "refine_project_all_cores_per_round": allc["wall_s"],
-                     "refine_per_round": allc["refine_s_max"],
-                     "project_per_round": allc["project_s_max"]},
+                     "refine_project_all_cores_per_wave": allc["wall_s"],
+                     "refine_per_wave": allc["refine_s_max"],
+                     "project_per_wave": allc["project_s_max"]},
         "one_core": {"value": full_updates / t_one, "cores": 1, "seconds_per_vcycle": t_one,
                      "sample": "the same V-cycle on one column in one process, scaled to %d "
                                "columns" % d},
