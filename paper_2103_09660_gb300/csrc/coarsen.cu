@@ -414,7 +414,8 @@ int coarsen_step(hnv_graph* g, int level, const hnv_coarsen_params* p,
   // the keys were packed hyperedge by hyperedge: sorting every hyperedge's
   // run by its low word gives what a full sort by (e, rep) would
   if (max_e_len <= kSegSortMax) {
-    HNV_CHECK(segmented_sort_low32(m, fine->e_ptr, (const int64_t*)nullptr, max_e_len, nnz, k0, s));
+    HNV_CHECK(segmented_sort_low32(m, fine->e_ptr, (const int64_t*)nullptr, max_e_len, nnz, k0, s,
+                                   (uint32_t)n2));
     sorted = k0;
   } else {
     int shifts[16];

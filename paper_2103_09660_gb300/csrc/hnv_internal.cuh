@@ -161,9 +161,16 @@ int bits_for_count(int64_t count);
 // bits (stable is irrelevant: keys within a segment share their high word).
 // ptr is int32 (ptr32) or int64 (ptr64, when ptr32 is null); max_len bounds
 // the segment lengths and must be <= kSegSortMax.
+// distinct_range > 0 promises that every low word is < distinct_range and
+// that the caller needs only each segment's sorted distinct values: segments
+// of more than 256 keys then hold their distinct values ascending followed by
+// copies of the largest (still sorted; only the multiplicities differ), when
+// a bitmap of distinct_range bits fits kSegBitmapBytes of shared memory.
 constexpr int32_t kSegSortMax = 8192;
+constexpr size_t kSegBitmapBytes = 160 * 1024;
 int segmented_sort_low32(int32_t segs, const int32_t* ptr32, const int64_t* ptr64,
-                         int32_t max_len, int64_t total_keys, uint64_t* keys, cudaStream_t s);
+                         int32_t max_len, int64_t total_keys, uint64_t* keys, cudaStream_t s,
+                         uint32_t distinct_range = 0);
 
 int fill_i32(int32_t* p, int32_t value, int64_t n, cudaStream_t s);
 

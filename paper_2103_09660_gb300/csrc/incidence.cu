@@ -694,7 +694,7 @@ int build_level0(hnv_graph* g, int32_t n, int32_t m, const int64_t* d_edge_ptr,
                    g->d_buf + 40));
   HNV_CHECK(read_ints(g, g->d_buf + 40, 1, &max_len, s));
   if (max_len <= kSegSortMax) {
-    HNV_CHECK(segmented_sort_low32(m, nullptr, d_edge_ptr, max_len, nnz_in, k0, s));
+    HNV_CHECK(segmented_sort_low32(m, nullptr, d_edge_ptr, max_len, nnz_in, k0, s, (uint32_t)n));
     sorted = k0;
   } else {
     int shifts[16];

@@ -111,12 +111,18 @@ rs_hist(const uint64_t* __restrict__ keys, int64_t n, int shift, int32_t* __rest
 }
 
 // Each warp ranks a contiguous run of 512 keys in order, so the tile's order
-// (warp, round, lane) is the input order and the scatter is stable.
+// (warp, round, lane) is the input order and the scatter is stable. The tile
+// is first reordered by digit in shared memory, so that the global writes go
+// out as runs of consecutive addresses (one run per digit) instead of one
+// scattered 8-byte store per key.
 __global__ void __launch_bounds__(RS_THREADS)
 rs_scatter(const uint64_t* __restrict__ keys, uint64_t* __restrict__ out, int64_t n, int shift,
            const int32_t* __restrict__ hist_scanned, int32_t ntiles) {
   __shared__ int32_t wcnt[RS_WARPS][256];
-  __shared__ int32_t toff[256];
+  __shared__ int32_t toff[256];    // first output position of digit d for this tile
+  __shared__ int32_t tstart[256];  // first tile position of digit d
+  __shared__ int32_t wsum[RS_WARPS];
+  __shared__ uint64_t stage[RS_TILE];
   for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) (&wcnt[0][0])[i] = 0;
   toff[threadIdx.x] = hist_scanned[(int64_t)threadIdx.x * ntiles + blockIdx.x];
   __syncthreads();
@@ -124,7 +130,8 @@ rs_scatter(const uint64_t* __restrict__ keys, uint64_t* __restrict__ out, int64_
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
-  const int64_t base = (int64_t)blockIdx.x * RS_TILE + (int64_t)w * (32 * RS_ITEMS);
+  const int64_t tile0 = (int64_t)blockIdx.x * RS_TILE;
+  const int64_t base = tile0 + (int64_t)w * (32 * RS_ITEMS);
   uint64_t kv[RS_ITEMS];
   int32_t loc[RS_ITEMS];
   int32_t dg[RS_ITEMS];
@@ -145,19 +152,36 @@ rs_scatter(const uint64_t* __restrict__ keys, uint64_t* __restrict__ out, int64_
     dg[j] = d;
   }
   __syncthreads();
-  {
-    int32_t run = 0;
+  // per digit (thread t = digit): warps' exclusive offsets, then the digit's
+  // tile start as an exclusive scan over digits (warp scans, then warp sums)
+  int32_t run = 0;
 #pragma unroll
-    for (int q = 0; q < RS_WARPS; ++q) {
-      int32_t c = wcnt[q][threadIdx.x];
-      wcnt[q][threadIdx.x] = run;
-      run += c;
-    }
+  for (int q = 0; q < RS_WARPS; ++q) {
+    const int32_t c = wcnt[q][threadIdx.x];
+    wcnt[q][threadIdx.x] = run;
+    run += c;
   }
+  int32_t inc = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t y = __shfl_up_sync(FULL, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) wsum[w] = inc;
+  __syncthreads();
+  int32_t before = 0;
+  for (int q = 0; q < w; ++q) before += wsum[q];
+  tstart[threadIdx.x] = before + inc - run;
   __syncthreads();
 #pragma unroll
-  for (int j = 0; j < RS_ITEMS; ++j) {
-    if (dg[j] < 256) out[toff[dg[j]] + wcnt[w][dg[j]] + loc[j]] = kv[j];
+  for (int j = 0; j < RS_ITEMS; ++j)
+    if (dg[j] < 256) stage[tstart[dg[j]] + wcnt[w][dg[j]] + loc[j]] = kv[j];
+  __syncthreads();
+  const int32_t count = (int32_t)(n - tile0 < RS_TILE ? n - tile0 : RS_TILE);
+  for (int32_t i = threadIdx.x; i < count; i += RS_THREADS) {
+    const uint64_t key = stage[i];
+    const int d = (int)((unsigned)(key >> shift) & 255u);
+    out[toff[d] + (i - tstart[d])] = key;
   }
 }
 
@@ -322,10 +346,72 @@ seg_sort_block(const int32_t* __restrict__ long_segs, const int32_t* __restrict_
   }
 }
 
+// The listed segments (more than 256 keys) when only their sorted distinct
+// low words matter and those lie in [0, range): one block each marks the
+// values in a shared-memory bitmap, then writes the set bits in ascending
+// order and fills the rest of the segment with copies of its largest value.
+// Linear in the segment and the bitmap, where the bitonic network of
+// seg_sort_block is O(len log^2 len) with a barrier per step.
+template <typename P>
+__global__ void __launch_bounds__(kSegThreads)
+seg_dedup_bitmap(const int32_t* __restrict__ long_segs, const int32_t* __restrict__ n_long,
+                 const P* __restrict__ e_ptr, uint64_t* __restrict__ keys, int32_t words) {
+  extern __shared__ uint32_t bm[];
+  __shared__ int32_t wsum[kSegThreads / 32];
+  __shared__ uint32_t vmax;
+  const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
+  // thread t owns bitmap words [t * per, min(words, (t + 1) * per))
+  const int32_t per = (words + kSegThreads - 1) / kSegThreads;
+  const int32_t w0 = min(words, (int32_t)threadIdx.x * per);
+  const int32_t w1 = min(words, w0 + per);
+  const int32_t count = *n_long;
+  for (int32_t q = blockIdx.x; q < count; q += gridDim.x) {
+    const int32_t e = long_segs[q];
+    const int64_t b = e_ptr[e];
+    const int32_t len = (int32_t)(e_ptr[e + 1] - b);
+    for (int32_t i = threadIdx.x; i < words; i += kSegThreads) bm[i] = 0u;
+    if (threadIdx.x == 0) vmax = 0u;
+    __syncthreads();
+    for (int32_t i = threadIdx.x; i < len; i += kSegThreads) {
+      const uint32_t v = (uint32_t)keys[b + i];
+      atomicOr(&bm[v >> 5], 1u << (v & 31));
+      atomicMax(&vmax, v);
+    }
+    __syncthreads();
+    int32_t c = 0;
+    for (int32_t i = w0; i < w1; ++i) c += __popc(bm[i]);
+    int32_t inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(FULL, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    int32_t off = inc - c;
+    for (int q2 = 0; q2 < w; ++q2) off += wsum[q2];
+    int32_t distinct = 0;
+    for (int q2 = 0; q2 < kSegThreads / 32; ++q2) distinct += wsum[q2];
+    const uint64_t hi = (uint64_t)(uint32_t)e << 32;
+    for (int32_t i = w0; i < w1; ++i) {
+      uint32_t bits = bm[i];
+      while (bits) {
+        const int t = __ffs(bits) - 1;
+        bits &= bits - 1u;
+        keys[b + off++] = hi | ((uint32_t)i * 32u + (uint32_t)t);
+      }
+    }
+    for (int32_t i = distinct + threadIdx.x; i < len; i += kSegThreads) keys[b + i] = hi | vmax;
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
 int segmented_sort_low32(int32_t segs, const int32_t* ptr32, const int64_t* ptr64,
-                         int32_t max_len, int64_t total_keys, uint64_t* keys, cudaStream_t s) {
+                         int32_t max_len, int64_t total_keys, uint64_t* keys, cudaStream_t s,
+                         uint32_t distinct_range) {
   if (max_len > kSegSortMax) HNV_FAIL(HNV_ERR_INVALID_ARG, "segment of %d keys", max_len);
   if (segs <= 0 || max_len < 2) return HNV_OK;
   TempPool pool(s);
@@ -335,20 +421,34 @@ int segmented_sort_low32(int32_t segs, const int32_t* ptr32, const int64_t* ptr6
   HNV_CUDA(cudaMemsetAsync(n_long, 0, sizeof(int32_t), s));
   const unsigned gw = grid_for((int64_t)segs * 32, 256);
   const unsigned gb = (unsigned)(4 * num_sms());
-  if (ptr32) {
+  const int32_t words = (int32_t)(((uint64_t)distinct_range + 31) / 32);
+  const bool bitmap = distinct_range > 0 && (size_t)words * 4 <= kSegBitmapBytes;
+  if (ptr32)
     HNV_CHECK(launch("seg_sort_warp", seg_sort_warp<int32_t>, gw, 256, 0, s, segs, ptr32, keys,
                      long_segs, n_long));
-    if (max_len > 256)
-      HNV_CHECK(launch("seg_sort_block", seg_sort_block<int32_t>, gb, kSegThreads, 0, s,
-                       (const int32_t*)long_segs, (const int32_t*)n_long, ptr32, keys));
-  } else {
+  else
     HNV_CHECK(launch("seg_sort_warp", seg_sort_warp<int64_t>, gw, 256, 0, s, segs, ptr64, keys,
                      long_segs, n_long));
-    if (max_len > 256)
-      HNV_CHECK(launch("seg_sort_block", seg_sort_block<int64_t>, gb, kSegThreads, 0, s,
-                       (const int32_t*)long_segs, (const int32_t*)n_long, ptr64, keys));
+  if (max_len <= 256) return HNV_OK;
+  if (bitmap) {
+    const size_t smem = (size_t)words * 4;
+    const unsigned gd = (unsigned)(num_sms() * (smem <= 48 * 1024 ? 4 : 1));
+    if (ptr32) {
+      HNV_CUDA(cudaFuncSetAttribute(seg_dedup_bitmap<int32_t>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      return launch("seg_dedup_bitmap", seg_dedup_bitmap<int32_t>, gd, kSegThreads, smem, s,
+                    (const int32_t*)long_segs, (const int32_t*)n_long, ptr32, keys, words);
+    }
+    HNV_CUDA(cudaFuncSetAttribute(seg_dedup_bitmap<int64_t>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return launch("seg_dedup_bitmap", seg_dedup_bitmap<int64_t>, gd, kSegThreads, smem, s,
+                  (const int32_t*)long_segs, (const int32_t*)n_long, ptr64, keys, words);
   }
-  return HNV_OK;
+  if (ptr32)
+    return launch("seg_sort_block", seg_sort_block<int32_t>, gb, kSegThreads, 0, s,
+                  (const int32_t*)long_segs, (const int32_t*)n_long, ptr32, keys);
+  return launch("seg_sort_block", seg_sort_block<int64_t>, gb, kSegThreads, 0, s,
+                (const int32_t*)long_segs, (const int32_t*)n_long, ptr64, keys);
 }
 
 int exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, int32_t* total,
