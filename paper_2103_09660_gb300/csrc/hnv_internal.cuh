@@ -157,6 +157,36 @@ int radix_shifts(int low_bits, int high_bits, int* shifts);
 // Number of bits needed to hold values in [0, count).
 int bits_for_count(int64_t count);
 
+// Visits every entry k of the rows [0, rows) of a CSR with offsets ptr as
+// f(row, k). A warp takes 32 consecutive rows, whose entries are contiguous,
+// and walks them 32 at a time (coalesced, every lane busy whatever the row
+// lengths), finding each entry's row by a binary search over the 32 row
+// starts held one per lane. Launch with one thread per row (any grid).
+template <typename P, typename F>
+__device__ __forceinline__ void csr_rows_warp_visit(int64_t rows, const P* __restrict__ ptr,
+                                                    F f) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t r0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32;
+       r0 < rows; r0 += warps * 32) {
+    const int64_t last = r0 + 32 < rows ? r0 + 32 : rows;
+    const int64_t mine = r0 + lane < last ? r0 + lane : last;
+    const int64_t start = (int64_t)ptr[mine];  // lanes past the last row hold the end
+    const int64_t first = __shfl_sync(0xffffffffu, start, 0);
+    const int64_t end = (int64_t)ptr[last];
+    for (int64_t base = first; base < end; base += 32) {
+      const int64_t k = base + lane;
+      int j = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int64_t sc = __shfl_sync(0xffffffffu, start, j + step);
+        if (sc <= k) j += step;
+      }
+      if (k < end) f(r0 + j, k);
+    }
+  }
+}
+
 // Sorts keys[ptr[i] .. ptr[i+1]) of every segment i < segs by their low 32
 // bits (stable is irrelevant: keys within a segment share their high word).
 // ptr is int32 (ptr32) or int64 (ptr64, when ptr32 is null); max_len bounds

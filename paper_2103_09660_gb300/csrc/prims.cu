@@ -195,17 +195,12 @@ __global__ void fill_i32_kernel(int32_t* p, int32_t v, int64_t n) {
     p[i] = v;
 }
 
-// key = (col << 32) | row for every CSR entry (warp per row).
+// key = (col << 32) | row for every CSR entry.
 __global__ void pack_col_row(int32_t n_rows, const int32_t* __restrict__ row_ptr,
                              const int32_t* __restrict__ cols, uint64_t* __restrict__ keys) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < n_rows;
-       r += warps) {
-    const int32_t b = row_ptr[r], e = row_ptr[r + 1];
-    for (int32_t k = b + lane; k < e; k += 32)
-      keys[k] = ((uint64_t)(uint32_t)cols[k] << 32) | (uint32_t)r;
-  }
+  csr_rows_warp_visit(n_rows, row_ptr, [&](int64_t r, int64_t k) {
+    keys[k] = ((uint64_t)(uint32_t)cols[k] << 32) | (uint32_t)r;
+  });
 }
 
 // col_ptr of keys sorted by their high word (the column): position i starts
@@ -284,26 +279,62 @@ __device__ __forceinline__ void warp_sort_segment(uint64_t* keys, int64_t b, int
   }
 }
 
-// Segments longer than 256 are appended to `long_segs` for seg_sort_block.
+// A lane sorts a segment of 2..8 keys by itself: Knuth's 19-comparator
+// network for 8 inputs over the low words, padded with 0xffffffff.
+__device__ __forceinline__ void lane_sort8(uint64_t* keys, int64_t b, int32_t len, uint32_t e) {
+  uint32_t x[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) x[i] = i < len ? (uint32_t)keys[b + i] : 0xffffffffu;
+#define HNV_CE(i, j)                       \
+  {                                        \
+    const uint32_t lo = min(x[i], x[j]);   \
+    x[j] = max(x[i], x[j]);                \
+    x[i] = lo;                             \
+  }
+  HNV_CE(0, 2) HNV_CE(1, 3) HNV_CE(4, 6) HNV_CE(5, 7)
+  HNV_CE(0, 4) HNV_CE(1, 5) HNV_CE(2, 6) HNV_CE(3, 7)
+  HNV_CE(0, 1) HNV_CE(2, 3) HNV_CE(4, 5) HNV_CE(6, 7)
+  HNV_CE(2, 4) HNV_CE(3, 5)
+  HNV_CE(1, 4) HNV_CE(3, 6)
+  HNV_CE(1, 2) HNV_CE(3, 4) HNV_CE(5, 6)
+#undef HNV_CE
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+    if (i < len) keys[b + i] = ((uint64_t)e << 32) | x[i];
+}
+
+// A warp takes 32 consecutive segments: each lane sorts its own if it has
+// 2..8 keys; the warp then sorts the ones of 9..256 keys together, one after
+// another; longer ones are appended to `long_segs` for the block kernels.
 template <typename P>
 __global__ void seg_sort_warp(int32_t m, const P* __restrict__ e_ptr,
                               uint64_t* __restrict__ keys, int32_t* __restrict__ long_segs,
                               int32_t* __restrict__ n_long) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); e < m;
-       e += warps) {
-    const int64_t b = e_ptr[e];
-    const int32_t len = (int32_t)(e_ptr[e + 1] - b);
-    if (len > 256) {                         // warp-uniform
-      if (lane == 0) long_segs[atomicAdd(n_long, 1)] = (int32_t)e;
-      continue;
+  for (int64_t e0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; e0 < m;
+       e0 += warps * 32) {
+    const int64_t e = e0 + lane;
+    int64_t b = 0;
+    int32_t len = 0;
+    if (e < m) {
+      b = e_ptr[e];
+      len = (int32_t)(e_ptr[e + 1] - b);
     }
-    if (len < 2) continue;
-    if (len <= 32) warp_sort_segment<1>(keys, b, len, (uint32_t)e, lane);
-    else if (len <= 64) warp_sort_segment<2>(keys, b, len, (uint32_t)e, lane);
-    else if (len <= 128) warp_sort_segment<4>(keys, b, len, (uint32_t)e, lane);
-    else warp_sort_segment<8>(keys, b, len, (uint32_t)e, lane);
+    if (len >= 2 && len <= 8) lane_sort8(keys, b, len, (uint32_t)e);
+    if (len > 256) long_segs[atomicAdd(n_long, 1)] = (int32_t)e;
+    unsigned mid = __ballot_sync(FULL, len > 8 && len <= 256);
+    while (mid) {
+      const int src = __ffs(mid) - 1;
+      mid &= mid - 1u;
+      const int64_t sb = __shfl_sync(FULL, b, src);
+      const int32_t sl = __shfl_sync(FULL, len, src);
+      const uint32_t se = (uint32_t)(e0 + src);
+      if (sl <= 32) warp_sort_segment<1>(keys, sb, sl, se, lane);
+      else if (sl <= 64) warp_sort_segment<2>(keys, sb, sl, se, lane);
+      else if (sl <= 128) warp_sort_segment<4>(keys, sb, sl, se, lane);
+      else warp_sort_segment<8>(keys, sb, sl, se, lane);
+    }
   }
 }
 
@@ -348,39 +379,59 @@ seg_sort_block(const int32_t* __restrict__ long_segs, const int32_t* __restrict_
 
 // The listed segments (more than 256 keys) when only their sorted distinct
 // low words matter and those lie in [0, range): one block each marks the
-// values in a shared-memory bitmap, then writes the set bits in ascending
-// order and fills the rest of the segment with copies of its largest value.
-// Linear in the segment and the bitmap, where the bitonic network of
-// seg_sort_block is O(len log^2 len) with a barrier per step.
-template <typename P>
+// values in a shared-memory bitmap (bm, one bit per value), then writes the
+// set bits in ascending order and fills the rest of the segment with copies
+// of its largest value: linear in the segment and the bitmap, where the
+// bitonic network of seg_sort_block is O(len log^2 len) with a barrier a
+// step. TWO_LEVEL (large ranges): a summary bitmap (sm, one bit per word of
+// bm) lets the scan skip empty words, and only the words a segment touched
+// are cleared after it, so the work per segment is linear in its length plus
+// range / 1024; otherwise every thread scans and clears its share of bm.
+template <typename P, bool TWO_LEVEL>
 __global__ void __launch_bounds__(kSegThreads)
 seg_dedup_bitmap(const int32_t* __restrict__ long_segs, const int32_t* __restrict__ n_long,
                  const P* __restrict__ e_ptr, uint64_t* __restrict__ keys, int32_t words) {
   extern __shared__ uint32_t bm[];
   __shared__ int32_t wsum[kSegThreads / 32];
   __shared__ uint32_t vmax;
+  const int32_t swords = TWO_LEVEL ? (words + 31) / 32 : 0;
+  uint32_t* sm = bm + words;
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
-  // thread t owns bitmap words [t * per, min(words, (t + 1) * per))
-  const int32_t per = (words + kSegThreads - 1) / kSegThreads;
-  const int32_t w0 = min(words, (int32_t)threadIdx.x * per);
-  const int32_t w1 = min(words, w0 + per);
+  // thread t owns scan words [t * per, min(nscan, (t + 1) * per)) of sm
+  // (TWO_LEVEL) or of bm
+  const int32_t nscan = TWO_LEVEL ? swords : words;
+  const int32_t per = (nscan + kSegThreads - 1) / kSegThreads;
+  const int32_t s0 = min(nscan, (int32_t)threadIdx.x * per);
+  const int32_t s1 = min(nscan, s0 + per);
+  for (int32_t i = threadIdx.x; i < words + swords; i += kSegThreads) bm[i] = 0u;
   const int32_t count = *n_long;
   for (int32_t q = blockIdx.x; q < count; q += gridDim.x) {
     const int32_t e = long_segs[q];
     const int64_t b = e_ptr[e];
     const int32_t len = (int32_t)(e_ptr[e + 1] - b);
-    for (int32_t i = threadIdx.x; i < words; i += kSegThreads) bm[i] = 0u;
     if (threadIdx.x == 0) vmax = 0u;
     __syncthreads();
     for (int32_t i = threadIdx.x; i < len; i += kSegThreads) {
       const uint32_t v = (uint32_t)keys[b + i];
       atomicOr(&bm[v >> 5], 1u << (v & 31));
+      if (TWO_LEVEL) atomicOr(&sm[v >> 10], 1u << ((v >> 5) & 31));
       atomicMax(&vmax, v);
     }
     __syncthreads();
     int32_t c = 0;
-    for (int32_t i = w0; i < w1; ++i) c += __popc(bm[i]);
+    for (int32_t i = s0; i < s1; ++i) {
+      if (TWO_LEVEL) {
+        uint32_t sbits = sm[i];
+        while (sbits) {
+          const int t = __ffs(sbits) - 1;
+          sbits &= sbits - 1u;
+          c += __popc(bm[i * 32 + t]);
+        }
+      } else {
+        c += __popc(bm[i]);
+      }
+    }
     int32_t inc = c;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -394,17 +445,44 @@ seg_dedup_bitmap(const int32_t* __restrict__ long_segs, const int32_t* __restric
     int32_t distinct = 0;
     for (int q2 = 0; q2 < kSegThreads / 32; ++q2) distinct += wsum[q2];
     const uint64_t hi = (uint64_t)(uint32_t)e << 32;
-    for (int32_t i = w0; i < w1; ++i) {
-      uint32_t bits = bm[i];
-      while (bits) {
-        const int t = __ffs(bits) - 1;
-        bits &= bits - 1u;
-        keys[b + off++] = hi | ((uint32_t)i * 32u + (uint32_t)t);
+    for (int32_t i = s0; i < s1; ++i) {
+      uint32_t sbits = TWO_LEVEL ? sm[i] : 1u;
+      while (sbits) {
+        const int t = __ffs(sbits) - 1;
+        sbits &= sbits - 1u;
+        const int32_t wi = TWO_LEVEL ? i * 32 + t : i;
+        uint32_t bits = bm[wi];
+        while (bits) {
+          const int u = __ffs(bits) - 1;
+          bits &= bits - 1u;
+          keys[b + off++] = hi | ((uint32_t)wi * 32u + (uint32_t)u);
+        }
       }
     }
     for (int32_t i = distinct + threadIdx.x; i < len; i += kSegThreads) keys[b + i] = hi | vmax;
     __syncthreads();
+    if (TWO_LEVEL) {
+      // clear what this segment set (values are re-read from the first
+      // `distinct` keys just written, all of them < range)
+      for (int32_t i = threadIdx.x; i < distinct; i += kSegThreads) {
+        const uint32_t v = (uint32_t)keys[b + i];
+        bm[v >> 5] = 0u;
+        sm[v >> 10] = 0u;
+      }
+    } else {
+      for (int32_t i = s0; i < s1; ++i) bm[i] = 0u;
+    }
+    __syncthreads();
   }
+}
+
+template <typename P, bool TWO>
+int launch_dedup(unsigned grid, size_t smem, cudaStream_t s, const int32_t* long_segs,
+                 const int32_t* n_long, const P* ptr, uint64_t* keys, int32_t words) {
+  HNV_CUDA(cudaFuncSetAttribute(seg_dedup_bitmap<P, TWO>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  return launch("seg_dedup_bitmap", seg_dedup_bitmap<P, TWO>, grid, kSegThreads, smem, s,
+                long_segs, n_long, ptr, keys, words);
 }
 
 }  // namespace
@@ -419,10 +497,11 @@ int segmented_sort_low32(int32_t segs, const int32_t* ptr32, const int64_t* ptr6
   HNV_CHECK(pool.get(&long_segs, (size_t)(total_keys / 257 + 1)));
   HNV_CHECK(pool.get(&n_long, 1));
   HNV_CUDA(cudaMemsetAsync(n_long, 0, sizeof(int32_t), s));
-  const unsigned gw = grid_for((int64_t)segs * 32, 256);
+  const unsigned gw = grid_for((int64_t)segs, 256);  // a warp per 32 segments
   const unsigned gb = (unsigned)(4 * num_sms());
   const int32_t words = (int32_t)(((uint64_t)distinct_range + 31) / 32);
-  const bool bitmap = distinct_range > 0 && (size_t)words * 4 <= kSegBitmapBytes;
+  const int32_t swords = (words + 31) / 32;
+  const bool bitmap = distinct_range > 0 && (size_t)(words + swords) * 4 <= kSegBitmapBytes;
   if (ptr32)
     HNV_CHECK(launch("seg_sort_warp", seg_sort_warp<int32_t>, gw, 256, 0, s, segs, ptr32, keys,
                      long_segs, n_long));
@@ -431,18 +510,15 @@ int segmented_sort_low32(int32_t segs, const int32_t* ptr32, const int64_t* ptr6
                      long_segs, n_long));
   if (max_len <= 256) return HNV_OK;
   if (bitmap) {
-    const size_t smem = (size_t)words * 4;
+    // the summary pays off once a thread would scan more than 8 words
+    const bool two = words > 8 * kSegThreads;
+    const size_t smem = (size_t)(words + (two ? swords : 0)) * 4;
     const unsigned gd = (unsigned)(num_sms() * (smem <= 48 * 1024 ? 4 : 1));
-    if (ptr32) {
-      HNV_CUDA(cudaFuncSetAttribute(seg_dedup_bitmap<int32_t>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      return launch("seg_dedup_bitmap", seg_dedup_bitmap<int32_t>, gd, kSegThreads, smem, s,
-                    (const int32_t*)long_segs, (const int32_t*)n_long, ptr32, keys, words);
-    }
-    HNV_CUDA(cudaFuncSetAttribute(seg_dedup_bitmap<int64_t>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    return launch("seg_dedup_bitmap", seg_dedup_bitmap<int64_t>, gd, kSegThreads, smem, s,
-                  (const int32_t*)long_segs, (const int32_t*)n_long, ptr64, keys, words);
+    if (ptr32)
+      return two ? launch_dedup<int32_t, true>(gd, smem, s, long_segs, n_long, ptr32, keys, words)
+                 : launch_dedup<int32_t, false>(gd, smem, s, long_segs, n_long, ptr32, keys, words);
+    return two ? launch_dedup<int64_t, true>(gd, smem, s, long_segs, n_long, ptr64, keys, words)
+               : launch_dedup<int64_t, false>(gd, smem, s, long_segs, n_long, ptr64, keys, words);
   }
   if (ptr32)
     return launch("seg_sort_block", seg_sort_block<int32_t>, gb, kSegThreads, 0, s,
@@ -525,7 +601,7 @@ int transpose_csr(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t* ro
   uint64_t *k0 = nullptr, *k1 = nullptr, *sorted = nullptr;
   HNV_CHECK(pool.get(&k0, (size_t)nnz));
   HNV_CHECK(pool.get(&k1, (size_t)nnz));
-  HNV_CHECK(launch("pack_col_row", pack_col_row, grid_for((int64_t)n_rows * 32, 256), 256, 0, s,
+  HNV_CHECK(launch("pack_col_row", pack_col_row, grid_for((int64_t)n_rows, 256), 256, 0, s,
                    n_rows, row_ptr, cols, k0));
   int shifts[16];
   int np = radix_shifts(0, bits_for_count(n_cols), shifts);
