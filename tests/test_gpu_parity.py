@@ -138,6 +138,29 @@ def test_long_rows_and_skew(H):
                     assert rel_err(_np(b), re) < FP32_TOL
 
 
+@pytest.mark.parametrize("n", [5000, 300000])
+def test_long_member_lists_with_repeats(H, n):
+    """Hyperedges of 300, 1000 and 6000 members drawn with replacement (many
+    repeats) among 4000 short ones, also with repeats. n = 5000 keeps the
+    distinct-value bitmaps of the member and image sorts flat; n = 300000
+    (most nodes alone) takes the two-level bitmap at the build and on the
+    coarse levels. The hierarchy must equal the oracle's bit for bit."""
+    rng = np.random.default_rng(11)
+    edges = [rng.integers(0, n, size) for size in (300, 1000, 6000)]
+    for _ in range(4000):
+        edges.append(rng.integers(0, min(n, 20000), int(rng.integers(2, 12))))
+    ptr = np.concatenate([[0], np.cumsum([len(e) for e in edges])]).astype(np.int64)
+    hg = hypergen.Hypergraph(n=n, m=len(edges), edge_ptr=ptr,
+                             edge_nodes=np.concatenate(edges).astype(np.int32),
+                             weights=rng.uniform(0.5, 2.0, len(edges)).astype(np.float32))
+    lv = oracle_level0(hg)
+    h = O.coarsen(lv, O.CoarsenParams(min_nodes=100, max_levels=3, seed=5))
+    for on_dev in (False, True):
+        with H.Graph.from_hypergraph(hg, on_device=on_dev) as G:
+            G.coarsen(min_nodes=100, max_levels=3, seed=5)
+            assert_hierarchy_equal(G, h)
+
+
 # ---------------------------------------------------------------------------
 # Refinement and projection
 # ---------------------------------------------------------------------------
