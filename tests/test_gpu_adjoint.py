@@ -48,10 +48,10 @@ def _gpu_grads(H, G, w0, zc, gv, ge, om, k):
     return gw.double().cpu().numpy(), gz.double().cpu().numpy(), zv, ze
 
 
-def _check_case(H, hg, seed, d=8, om=0.5, k=3, min_nodes=2):
+def _check_case(H, hg, seed, d=8, om=0.5, k=3, min_nodes=2, need_dw=False, max_levels=32):
     rng = np.random.default_rng(seed)
     lv0 = oracle_level0(hg)
-    h = O.coarsen(lv0, O.CoarsenParams(min_nodes=min_nodes, seed=seed))
+    h = O.coarsen(lv0, O.CoarsenParams(min_nodes=min_nodes, max_levels=max_levels, seed=seed))
     top = h.levels[-1]
     w0 = rng.uniform(0.5, 2.0, lv0.m).astype(np.float32).astype(np.float64)
     zc = rng.standard_normal((top.n + top.m, d)).astype(np.float32).astype(np.float64)
@@ -59,8 +59,10 @@ def _check_case(H, hg, seed, d=8, om=0.5, k=3, min_nodes=2):
     ge = rng.standard_normal((lv0.m, d)).astype(np.float32).astype(np.float64)
     hw = O.with_weights(h, w0)
     dw_ref, dz_ref = O.vcycle_grad(hw, zc, om, k, gv, ge)
+    if need_dw:  # the case must exercise the weight gradients
+        assert np.abs(dw_ref).max() > 1e-3 * np.abs(gv).max() * np.abs(zc).max()
     with H.Graph.from_hypergraph(hg) as G:
-        G.coarsen(min_nodes=min_nodes, seed=seed)
+        G.coarsen(min_nodes=min_nodes, max_levels=max_levels, seed=seed)
         dw, dz, zv, ze = _gpu_grads(H, G, w0, zc, gv, ge, om, k)
         # the checkpointed forward is the plain V-cycle with these weights
         ref = O.vcycle(hw, zc, om, k)
@@ -92,10 +94,16 @@ def test_adjoint_omega_extremes(H):
     """omega near 0, where z~_v = s_v / D_v carries a weight gradient of
     size omega and must not be recovered from consecutive iterates (which
     would leave eps |z| / omega of error in it); omega = 1 (z_v^i = z~_v);
-    omega = 0 (every sweep the identity, weight gradients exactly zero)."""
-    for i, hg in enumerate(small_cases(12, 15, n_max=30, m_max=20)):
+    omega = 0 (every sweep the identity, weight gradients exactly zero).
+    The graphs are coarsened only to 8 nodes or 4 levels so that the coarsest
+    level keeps hyperedges and the weight gradients do not vanish."""
+    for i in range(6):
+        rng = np.random.default_rng(100 + i)
+        hg = hypergen.random_small_hypergraph(rng, 30 + 2 * i, 24 + i, max_size=5,
+                                              weighted=True)
         for om in (0.02, 0.001, 1.0, 0.0):
-            _check_case(H, hg, seed=100 + i, d=8, om=om, k=3)
+            _check_case(H, hg, seed=100 + i, d=8, om=om, k=3, min_nodes=8, max_levels=4,
+                        need_dw=om > 0)
 
 
 def test_adjoint_skewed_split_rows(H):
