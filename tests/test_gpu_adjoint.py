@@ -85,9 +85,14 @@ def _check_case(H, hg, seed, d=8, om=0.5, k=3, min_nodes=2, need_dw=False, max_l
 
 
 def test_adjoint_small_random_graphs(H):
+    """Random small graphs, coarsened to 2 nodes (the deepest hierarchies;
+    their weight gradients are often zero, see test_adjoint_omega_extremes)
+    and to 8 nodes or 4 levels (coarsest levels with hyperedges)."""
     for i, hg in enumerate(small_cases(40, 15, n_max=30, m_max=20)):
         for om in (0.5, 0.3):
             _check_case(H, hg, seed=i, d=4 * (1 + i % 3), om=om, k=2 + i % 3)
+            _check_case(H, hg, seed=i, d=4 * (1 + i % 3), om=om, k=2 + i % 3, min_nodes=8,
+                        max_levels=4)
 
 
 def test_adjoint_omega_extremes(H):
